@@ -1,0 +1,214 @@
+/*
+ * dock.h -- C ABI of the GB300 docking library (libdock.so, CUDA sm_103a).
+ *
+ * The library evaluates and optimises ligand poses against receptor grids:
+ * the population-parallel pose evaluation inside a Lamarckian genetic search
+ * (paper, Section II-A).  A genotype is
+ *     [ t_x, t_y, t_z,  q_w, q_x, q_y, q_z,  tau_0 ... tau_{T-1} ]   (FP32)
+ * G = 7 + T genes: translation of the ligand centroid (A), an orientation
+ * quaternion (any non-zero norm; normalised on use), and one torsion angle
+ * (radians, relative to the input conformation) per rotatable bond, in the
+ * order the rotatable bonds appear in the bond list given to load_ligand.
+ *
+ * Conventions for every entry point:
+ *   - return 0 (DOCK_OK) or a negative DOCK_ERR_* code; nothing aborts the
+ *     process; dock_last_error(ctx) gives a one-line description;
+ *   - "host" pointers are read or written before the call returns;
+ *   - "device" pointers are CUDA device memory owned by the caller, used in
+ *     stream order on the given stream (cudaStream_t passed as void*, NULL =
+ *     the legacy default stream); the call returns once the work is queued;
+ *   - handles (dock_ctx, dock_grids, dock_ligand) are owned by the library
+ *     and released by the matching free call; a handle is used by one host
+ *     thread at a time.
+ * All arithmetic on the device is FP32, except the FP64 re-scoring of each
+ * run's best pose in dock()/dock_async().
+ */
+#ifndef GB300_DOCK_H
+#define GB300_DOCK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DOCK_OK 0
+#define DOCK_ERR_INVALID (-1)      /* bad argument (null, size, range)             */
+#define DOCK_ERR_CUDA (-2)         /* a CUDA runtime call failed                   */
+#define DOCK_ERR_OOM (-3)          /* device allocation failed                     */
+#define DOCK_ERR_DISCONNECTED (-4) /* ligand bond graph is not connected           */
+#define DOCK_ERR_RING (-5)         /* a rotatable bond lies in a ring              */
+#define DOCK_ERR_SIZE (-6)         /* too many atoms (>255) or torsions (>32)      */
+#define DOCK_ERR_TYPE (-7)         /* unknown atom type code                       */
+#define DOCK_ERR_NOMAP (-8)        /* a ligand atom type has no map in the grids   */
+#define DOCK_ERR_DEVICE (-9)       /* a kernel reported an error through its flag  */
+
+#define DOCK_MAX_ATOMS 255
+#define DOCK_MAX_TORSIONS 32
+
+/* Atom type codes (ligand and receptor): C, A (aromatic C), N, NA (acceptor
+ * N), OA (acceptor O), SA (acceptor S), HD (donor H). */
+enum { DOCK_C = 0, DOCK_A = 1, DOCK_N = 2, DOCK_NA = 3, DOCK_OA = 4, DOCK_SA = 5, DOCK_HD = 6, DOCK_NTYPES = 7 };
+/* map_type codes for the two charge maps in load_grids */
+#define DOCK_MAP_ELEC (-1)
+#define DOCK_MAP_DESOLV (-2)
+
+typedef struct dock_ctx dock_ctx;
+typedef struct dock_grids dock_grids;
+typedef struct dock_ligand dock_ligand;
+
+/* Optional device allocator.  alloc returns device memory of >= bytes,
+ * 256-byte aligned, usable on `stream`, or NULL; free releases it.  With no
+ * allocator the library uses cudaMalloc / cudaFree. */
+typedef struct {
+    void *(*alloc)(size_t bytes, void *stream, void *user);
+    void (*free)(void *ptr, void *stream, void *user);
+    void *user;
+} dock_allocator;
+
+/* Search parameters (paper, Section II-A: population 150, crossover,
+ * fitness-based selection, local search on a random sample of each
+ * generation; the rates and the ADADELTA constants are this library's). */
+typedef struct {
+    int pop_size;      /* individuals per run (>= 2), default 150                  */
+    int nruns;         /* independent runs, default 10                              */
+    int64_t max_evals; /* per-run evaluation budget, default 100000                 */
+    int ls_count;      /* local searches per generation; default ceil(6% pop_size)  */
+    int ls_iters;      /* ADADELTA iterations per local search, default 100         */
+    float rho, eps;    /* ADADELTA decay and conditioner, default 0.8, 1e-2         */
+    float p_tour;      /* probability the fitter of two wins a tournament, 0.6      */
+    float p_cross;     /* two-point crossover probability, 0.8                      */
+    float p_mut;       /* per-gene-block mutation probability, 0.02                 */
+    float trans_mut;   /* translation mutation half-width (A), 2.0                  */
+} dock_params;
+
+/* Library version (major*10000 + minor*100 + patch). */
+int dock_version(void);
+
+/* Fills *p with the defaults listed in dock_params. */
+void dock_default_params(dock_params *p);
+
+/* Creates a context on CUDA device `device`.  alloc may be NULL. */
+int dock_create(dock_ctx **out, int device, const dock_allocator *alloc);
+/* Releases the context; grids and ligands must be freed first. */
+int dock_destroy(dock_ctx *ctx);
+/* One-line description of the last error on this context ("" if none). */
+const char *dock_last_error(const dock_ctx *ctx);
+
+/* ---- receptor grids: the "reaction field for the protein" (Section II-A) ----
+ * maps: host, [n_maps][dims[2]][dims[1]][dims[0]] FP32, x fastest; node
+ * (i,j,k) sits at origin + (i,j,k)*spacing.  map_type[m] is the ligand atom
+ * type served by map m, or DOCK_MAP_ELEC (potential per unit ligand charge)
+ * or DOCK_MAP_DESOLV (desolvation per unit |charge|); exactly one of each.
+ * An atom of type t and charge q at x scores M_t(x) + q E(x) + |q| D(x),
+ * read by trilinear interpolation; outside the box the read is clamped and
+ * 10 kcal/mol/A^2 times the squared distance outside is added per axis.
+ * The library keeps its own device copy.  Errors: dims < 2, spacing <= 0,
+ * non-finite values, duplicate or missing charge maps, OOM. */
+int load_grids(dock_ctx *ctx, const float *maps, int n_maps, const int dims[3], const double origin[3],
+               double spacing, const int *map_type, dock_grids **out);
+
+/* Builds the maps on the device from receptor atoms (host arrays: xyz
+ * [n_rec][3] A, type codes, partial charges), for ligand types
+ * map_types[0..n_type_maps), plus the electrostatic and desolvation maps:
+ * the direct sum over all receptor atoms of the same pair terms the ligand
+ * uses internally (no cutoff), type maps capped at +1e5 kcal/mol. */
+int build_grids(dock_ctx *ctx, int n_rec, const double *rxyz, const int *rtype, const double *rq,
+                const int dims[3], const double origin[3], double spacing, int n_type_maps,
+                const int *map_types, dock_grids **out);
+
+/* Copies the node values of a grid set back to host memory in the layout of
+ * load_grids (n_maps = n_type_maps + 2 for build_grids: type maps in the
+ * order given, then electrostatic, then desolvation). */
+int grids_read_maps(dock_ctx *ctx, const dock_grids *grids, float *maps_out);
+int free_grids(dock_ctx *ctx, dock_grids *grids);
+
+/* ---- ligand (Section II-A: atoms; rotatable bonds and rigid-body motion as
+ * the degrees of freedom) ----
+ * Host inputs: xyz [n_atoms][3] (A, the conformation at tau = 0), type codes,
+ * partial charges, bonds [n_bonds][2] atom indices, rotatable[n_bonds] 0/1.
+ * Builds on the host the rigid fragments, the torsion tree (root = largest
+ * fragment), the pair list (atoms in different fragments, >= 4 bonds apart)
+ * with per-pair coefficients, and uploads them.  Errors: n_atoms out of
+ * 1..255, > 32 rotatable bonds, unknown type, bad bond index, disconnected
+ * graph, rotatable bond in a ring, OOM. */
+int load_ligand(dock_ctx *ctx, int n_atoms, const double *xyz, const int *type, const double *charge,
+                int n_bonds, const int *bonds, const int *rotatable, dock_ligand **out);
+/* Sizes of a loaded ligand (any pointer may be NULL). */
+int ligand_info(const dock_ligand *lig, int *n_atoms, int *n_torsions, int *n_genes, int *n_pairs,
+                int *n_fragments);
+int free_ligand(dock_ctx *ctx, dock_ligand *lig);
+
+/* ---- batched evaluation (spec: score_batch, score_grad_batch) ----
+ * geno: device [B][G] FP32.  E: device [B] FP32 energies (kcal/mol).
+ * grad: device [B][G] FP32, dE/dgenotype (the quaternion part is the
+ * derivative through the normalisation, so it is orthogonal to q).
+ * Every ligand atom type must have a map (DOCK_ERR_NOMAP).  B = 0 is a
+ * no-op.  Deterministic: the same inputs give bit-identical outputs. */
+int score_batch(dock_ctx *ctx, const dock_grids *grids, const dock_ligand *lig, const float *geno, int B,
+                float *E, void *stream);
+int score_grad_batch(dock_ctx *ctx, const dock_grids *grids, const dock_ligand *lig, const float *geno, int B,
+                     float *E, float *grad, void *stream);
+/* Atom coordinates of each genotype (Section IV-B: atom rotations along the
+ * torsion tree), device [B][n_atoms][3] FP32 in input atom order. */
+int pose_batch(dock_ctx *ctx, const dock_ligand *lig, const float *geno, int B, float *xyz, void *stream);
+
+/* ---- the Lamarckian GA (Section II-A) ----
+ * Runs params->nruns independent searches of params->pop_size individuals
+ * until each has spent params->max_evals evaluations (checked at generation
+ * boundaries).  Per generation: elitism, tournament selection, two-point
+ * crossover, mutation, evaluation of the new individuals; ADADELTA on
+ * ls_count individuals drawn without replacement, best point written back;
+ * the per-run evaluation count grows by (pop_size-1) + ls_count*ls_iters.
+ * Random numbers: Philox4x32-10 keyed by seed, counter (purpose<<16|draw,
+ * individual, generation, run).  Deterministic for a given seed.
+ * dock(): host outputs best_geno [nruns][G] (unit quaternion), best_E
+ * [nruns] (FP64 re-score of best_geno), evals_used [nruns]; blocks until
+ * done.  dock_async(): the same into device buffers (best_E32: the FP32
+ * energy the search kept), queued on `stream`. */
+int dock(dock_ctx *ctx, const dock_grids *grids, const dock_ligand *lig, const dock_params *params, uint64_t seed,
+         float *best_geno, double *best_E, int64_t *evals_used);
+int dock_async(dock_ctx *ctx, const dock_grids *grids, const dock_ligand *lig, const dock_params *params,
+               uint64_t seed, float *best_geno, float *best_E32, double *best_E, int64_t *evals_used, void *stream);
+
+/* ---- operator-level entry points (the steps dock() composes) ---- all
+ * pointers device, FP32 genes, runs r = 0..nruns-1 laid out [nruns][pop][G].
+ * dock_init_population: generation-0 individuals (translation uniform in
+ * the grid box, orientation uniform on the unit 3-sphere, torsions uniform
+ * in [-pi, pi)); no evaluation.
+ * dock_ga_children: next generation from pop_old/E_old (slot 0 = the best
+ * old individual); no evaluation.  info (optional) [nruns][pop][5] int64:
+ * parent 1, parent 2, crossover cut lo, cut hi, mutated-block mask.
+ * dock_ls_picks: picks [nruns][n_ls], the individuals given a local search.
+ * dock_local_search: ADADELTA from B start points x0 [B][G], iters
+ * iterations each; x_best [B][G] (unit quaternion) and E_best [B].
+ * dock_philox: out[n][4] = Philox4x32-10(ctr[n][4], key = (key_lo, key_hi)). */
+int dock_init_population(dock_ctx *ctx, const dock_grids *grids, int n_torsions, int pop, int nruns,
+                         uint64_t seed, float *pop_out, void *stream);
+int dock_ga_children(dock_ctx *ctx, int n_torsions, int pop, int nruns, const float *pop_old, const float *E_old,
+                     uint64_t seed, uint32_t generation, const dock_params *params, float *pop_new,
+                     int64_t *info, void *stream);
+int dock_ls_picks(dock_ctx *ctx, int pop, int n_ls, int nruns, uint64_t seed, uint32_t generation, int *picks,
+                  void *stream);
+int dock_local_search(dock_ctx *ctx, const dock_grids *grids, const dock_ligand *lig, const float *x0, int B,
+                      int iters, float rho, float eps, float *x_best, float *E_best, void *stream);
+int dock_philox(dock_ctx *ctx, const uint32_t *ctr, int n, uint32_t key_lo, uint32_t key_hi, uint32_t *out,
+                void *stream);
+
+/* ---- tracing ----
+ * With timing on, every kernel launch of dock/dock_async/score_* is
+ * bracketed by CUDA events on its stream; dock_kernel_time() returns the
+ * summed device time and launch count per kernel name ("dock_ls",
+ * "dock_ga", "dock_init", "score", "score_grad", ...) since the last reset
+ * (it synchronises the context's events).  dock_launch_count() counts every
+ * kernel this context launched. */
+int dock_set_timing(dock_ctx *ctx, int enable);
+int dock_kernel_time(dock_ctx *ctx, const char *kernel, double *total_ms, int64_t *launches);
+int dock_reset_timing(dock_ctx *ctx);
+int64_t dock_launch_count(const dock_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GB300_DOCK_H */

@@ -78,6 +78,7 @@ def _L():
             "orc_score": (d, [vp, P(Grid), vp, vp, vp, vp]),
             "orc_score_batch": (i, [vp, P(Grid), vp, i, vp, vp, i]),
             "orc_pose_margins": (None, [vp, P(Grid), vp, vp]),
+            "orc_atom_forces": (d, [vp, P(Grid), vp, vp]),
             "orc_philox": (None, [vp, vp, vp]),
             "orc_init_individual": (None, [i, P(Grid), u64, u32, u32, vp]),
             "orc_init_population": (None, [i, P(Grid), u64, u32, i, vp]),
@@ -285,6 +286,12 @@ class OracleLigand:
         _L().orc_score_batch(self.h, grid.ref, _p(g), B, _p(E), _p(gr) if with_grad else None,
                              int(nthreads or os.cpu_count() or 1))
         return (E, gr) if with_grad else E
+
+    def atom_forces(self, grid, geno):
+        g = _f64(geno)
+        f = np.zeros((self.n_atoms, 3))
+        e = _L().orc_atom_forces(self.h, grid.ref, _p(g), _p(f))
+        return e, f
 
     def margins(self, grid, geno):
         g = _f64(geno)

@@ -89,20 +89,22 @@ static int is_hbond(int ta, int tb) {
  * minimum -ehb at Rhb of the acceptor; weights included. */
 double orc_vdw_hb(int ta, int tb, double r, double *dEdr) {
     double re = r < R_FLOOR ? R_FLOOR : r;
+    double r2 = re * re, r6 = r2 * r2 * r2, r10 = r6 * r2 * r2, r12 = r6 * r6; /* re^n */
     double e, d;
     if (is_hbond(ta, tb)) {
         const orc_type_t *acc = OT[ta].hb == 2 ? &OT[ta] : &OT[tb];
-        double c12 = 5.0 * acc->ehb * pow(acc->Rhb, 12.0);
-        double c10 = 6.0 * acc->ehb * pow(acc->Rhb, 10.0);
-        e = W_HB * (c12 / pow(re, 12.0) - c10 / pow(re, 10.0));
-        d = W_HB * (-12.0 * c12 / pow(re, 13.0) + 10.0 * c10 / pow(re, 11.0));
+        double R2 = acc->Rhb * acc->Rhb, R10 = R2 * R2 * R2 * R2 * R2;
+        double c12 = 5.0 * acc->ehb * R10 * R2;
+        double c10 = 6.0 * acc->ehb * R10;
+        e = W_HB * (c12 / r12 - c10 / r10);
+        d = W_HB * (-12.0 * c12 / (r12 * re) + 10.0 * c10 / (r10 * re));
     } else {
-        double R = 0.5 * (OT[ta].R + OT[tb].R);
+        double R = 0.5 * (OT[ta].R + OT[tb].R), R6 = R * R * R * R * R * R;
         double eps = sqrt(OT[ta].eps * OT[tb].eps);
-        double c12 = eps * pow(R, 12.0);
-        double c6 = 2.0 * eps * pow(R, 6.0);
-        e = W_VDW * (c12 / pow(re, 12.0) - c6 / pow(re, 6.0));
-        d = W_VDW * (-12.0 * c12 / pow(re, 13.0) + 6.0 * c6 / pow(re, 7.0));
+        double c12 = eps * R6 * R6;
+        double c6 = 2.0 * eps * R6;
+        e = W_VDW * (c12 / r12 - c6 / r6);
+        d = W_VDW * (-12.0 * c12 / (r12 * re) + 6.0 * c6 / (r6 * re));
     }
     if (dEdr) *dEdr = r < R_FLOOR ? 0.0 : d;
     return e;
@@ -1065,4 +1067,14 @@ int orc_score_batch(const orc_lig *L, const orc_grid *g, const float *geno, int 
 
 void orc_init_population(int nt, const orc_grid *g, uint64_t seed, uint32_t run, int pop, float *out) {
     for (int s = 0; s < pop; ++s) orc_init_individual(nt, g, seed, run, (uint32_t)s, out + (size_t)s * (7 + nt));
+}
+
+/* dE/dx_i of every atom (input order, [n][3]) at the pose of a genotype;
+ * returns E.  Used to bound how much an FP32 rounding of the atom positions
+ * can move the energy: |dE| <= sum_i |f_i|_1 * |dx|_max. */
+double orc_atom_forces(const orc_lig *L, const orc_grid *g, const double *geno, double *f_out) {
+    double x[ORC_MAX_ATOMS * 3];
+    orc_pose(L, geno, x);
+    memset(f_out, 0, sizeof(double) * 3 * L->n);
+    return orc_inter_xyz(L, g, x, f_out) + orc_intra_xyz(L, x, f_out);
 }

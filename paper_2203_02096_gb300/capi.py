@@ -1,0 +1,374 @@
+"""Python binding of libdock.so (include/dock.h): argument marshalling only.
+
+Every entry point keeps the C name.  Device buffers are torch CUDA tensors
+(passed by data pointer, no copies); device memory the library allocates
+comes from torch's caching allocator through the ``dock_allocator``
+callbacks; streams are torch streams.  Loading raises if libdock.so is
+missing or CUDA is unavailable -- there is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+DOCK_OK = 0
+ERRORS = {-1: "DOCK_ERR_INVALID", -2: "DOCK_ERR_CUDA", -3: "DOCK_ERR_OOM", -4: "DOCK_ERR_DISCONNECTED",
+          -5: "DOCK_ERR_RING", -6: "DOCK_ERR_SIZE", -7: "DOCK_ERR_TYPE", -8: "DOCK_ERR_NOMAP", -9: "DOCK_ERR_DEVICE"}
+MAP_ELEC, MAP_DESOLV = -1, -2
+
+# Every symbol include/dock.h declares, with (restype, argtypes).
+_vp, _i, _d, _f = C.c_void_p, C.c_int, C.c_double, C.c_float
+_u32, _u64, _i64, _sz = C.c_uint32, C.c_uint64, C.c_int64, C.c_size_t
+_P = C.POINTER
+
+
+class DockParams(C.Structure):
+    _fields_ = [("pop_size", _i), ("nruns", _i), ("max_evals", _i64), ("ls_count", _i), ("ls_iters", _i),
+                ("rho", _f), ("eps", _f), ("p_tour", _f), ("p_cross", _f), ("p_mut", _f), ("trans_mut", _f)]
+
+
+ALLOC_FN = C.CFUNCTYPE(_vp, _sz, _vp, _vp)
+FREE_FN = C.CFUNCTYPE(None, _vp, _vp, _vp)
+
+
+class DockAllocator(C.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("user", _vp)]
+
+
+SIGNATURES = {
+    "dock_version": (_i, []),
+    "dock_default_params": (None, [_P(DockParams)]),
+    "dock_create": (_i, [_P(_vp), _i, _P(DockAllocator)]),
+    "dock_destroy": (_i, [_vp]),
+    "dock_last_error": (C.c_char_p, [_vp]),
+    "load_grids": (_i, [_vp, _vp, _i, _vp, _vp, _d, _vp, _P(_vp)]),
+    "build_grids": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _vp, _d, _i, _vp, _P(_vp)]),
+    "grids_read_maps": (_i, [_vp, _vp, _vp]),
+    "free_grids": (_i, [_vp, _vp]),
+    "load_ligand": (_i, [_vp, _i, _vp, _vp, _vp, _i, _vp, _vp, _P(_vp)]),
+    "ligand_info": (_i, [_vp, _P(_i), _P(_i), _P(_i), _P(_i), _P(_i)]),
+    "free_ligand": (_i, [_vp, _vp]),
+    "score_batch": (_i, [_vp, _vp, _vp, _vp, _i, _vp, _vp]),
+    "score_grad_batch": (_i, [_vp, _vp, _vp, _vp, _i, _vp, _vp, _vp]),
+    "pose_batch": (_i, [_vp, _vp, _vp, _i, _vp, _vp]),
+    "dock": (_i, [_vp, _vp, _vp, _P(DockParams), _u64, _vp, _vp, _vp]),
+    "dock_async": (_i, [_vp, _vp, _vp, _P(DockParams), _u64, _vp, _vp, _vp, _vp, _vp]),
+    "dock_init_population": (_i, [_vp, _vp, _i, _i, _i, _u64, _vp, _vp]),
+    "dock_ga_children": (_i, [_vp, _i, _i, _i, _vp, _vp, _u64, _u32, _P(DockParams), _vp, _vp, _vp]),
+    "dock_ls_picks": (_i, [_vp, _i, _i, _i, _u64, _u32, _vp, _vp]),
+    "dock_local_search": (_i, [_vp, _vp, _vp, _vp, _i, _i, _f, _f, _vp, _vp, _vp]),
+    "dock_philox": (_i, [_vp, _vp, _i, _u32, _u32, _vp, _vp]),
+    "dock_set_timing": (_i, [_vp, _i]),
+    "dock_kernel_time": (_i, [_vp, C.c_char_p, _P(_d), _P(_i64)]),
+    "dock_reset_timing": (_i, [_vp]),
+    "dock_launch_count": (_i64, [_vp]),
+}
+
+
+def lib_path() -> str:
+    return _build.OUT
+
+
+def load(build_if_missing: bool = True):
+    """Load libdock.so (compiling it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build() if build_if_missing else _build.OUT
+            if not os.path.exists(path):
+                raise RuntimeError(f"libdock.so not found at {path}: the CUDA library must be built")
+            lib = C.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+class DockError(RuntimeError):
+    pass
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, torch.Tensor):
+        if not t.is_cuda:
+            raise ValueError("expected a CUDA tensor")
+        if not t.is_contiguous():
+            raise ValueError("expected a contiguous tensor")
+        return C.c_void_p(t.data_ptr())
+    return t.ctypes.data_as(C.c_void_p)
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def default_params(**kw) -> DockParams:
+    p = DockParams()
+    load().dock_default_params(C.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+class Context:
+    """dock_ctx bound to a CUDA device, device memory from torch's allocator."""
+
+    def __init__(self, device: int = 0, use_torch_allocator: bool = True):
+        if not torch.cuda.is_available():
+            raise RuntimeError("CUDA is not available: libdock has no CPU path")
+        self.lib = load()
+        self.device = device
+        torch.cuda.set_device(device)
+        self._cb = None
+        alloc = None
+        if use_torch_allocator:
+            def _alloc(nbytes, stream, user):
+                try:
+                    return torch.cuda.caching_allocator_alloc(int(nbytes), device, stream=int(stream or 0))
+                except Exception:  # reported to the caller as DOCK_ERR_OOM
+                    return None
+
+            def _free(ptr, stream, user):
+                torch.cuda.caching_allocator_delete(int(ptr))
+
+            self._cb = (ALLOC_FN(_alloc), FREE_FN(_free))
+            alloc = DockAllocator(self._cb[0], self._cb[1], None)
+        h = C.c_void_p()
+        rc = self.lib.dock_create(C.byref(h), device, C.byref(alloc) if alloc is not None else None)
+        if rc != DOCK_OK:
+            raise DockError(f"dock_create failed: {ERRORS.get(rc, rc)}")
+        self.h = h
+
+    def check(self, rc, what):
+        if rc != DOCK_OK:
+            msg = self.lib.dock_last_error(self.h).decode()
+            raise DockError(f"{what}: {ERRORS.get(rc, rc)}: {msg}")
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            torch.cuda.synchronize(self.device)
+            self.lib.dock_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- tracing
+    def set_timing(self, on: bool):
+        self.check(self.lib.dock_set_timing(self.h, int(on)), "dock_set_timing")
+
+    def reset_timing(self):
+        self.check(self.lib.dock_reset_timing(self.h), "dock_reset_timing")
+
+    def kernel_time(self, name: str):
+        ms, n = C.c_double(), C.c_int64()
+        self.check(self.lib.dock_kernel_time(self.h, name.encode(), C.byref(ms), C.byref(n)), "dock_kernel_time")
+        return ms.value, n.value
+
+    def launch_count(self) -> int:
+        return int(self.lib.dock_launch_count(self.h))
+
+
+class Grids:
+    def __init__(self, ctx: Context, h, n_maps: int):
+        self.ctx, self.h, self.n_maps = ctx, h, n_maps
+
+    def read_maps(self, dims):
+        nx, ny, nz = dims
+        out = np.zeros((self.n_maps, nz, ny, nx), dtype=np.float32)
+        self.ctx.check(self.ctx.lib.grids_read_maps(self.ctx.h, self.h, _ptr(out)), "grids_read_maps")
+        return out
+
+    def free(self):
+        if self.h is not None and self.ctx.h is not None:
+            self.ctx.lib.free_grids(self.ctx.h, self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def load_grids(ctx: Context, maps: np.ndarray, dims, origin, spacing: float, map_type) -> Grids:
+    maps = np.ascontiguousarray(maps, dtype=np.float32)
+    d = np.ascontiguousarray(dims, dtype=np.int32)
+    o = np.ascontiguousarray(origin, dtype=np.float64)
+    mt = np.ascontiguousarray(map_type, dtype=np.int32)
+    h = C.c_void_p()
+    ctx.check(ctx.lib.load_grids(ctx.h, _ptr(maps), len(mt), _ptr(d), _ptr(o), float(spacing), _ptr(mt), C.byref(h)),
+              "load_grids")
+    return Grids(ctx, h, len(mt))
+
+
+def build_grids(ctx: Context, rxyz, rtype, rq, dims, origin, spacing: float, map_types) -> Grids:
+    rx = np.ascontiguousarray(rxyz, dtype=np.float64)
+    rt = np.ascontiguousarray(rtype, dtype=np.int32)
+    q = np.ascontiguousarray(rq, dtype=np.float64)
+    d = np.ascontiguousarray(dims, dtype=np.int32)
+    o = np.ascontiguousarray(origin, dtype=np.float64)
+    mt = np.ascontiguousarray(map_types, dtype=np.int32)
+    h = C.c_void_p()
+    ctx.check(ctx.lib.build_grids(ctx.h, len(rt), _ptr(rx), _ptr(rt), _ptr(q), _ptr(d), _ptr(o), float(spacing),
+                                  len(mt), _ptr(mt), C.byref(h)), "build_grids")
+    return Grids(ctx, h, len(mt) + 2)
+
+
+class Ligand:
+    def __init__(self, ctx: Context, h):
+        self.ctx, self.h = ctx, h
+        v = [C.c_int() for _ in range(5)]
+        ctx.check(ctx.lib.ligand_info(h, *[C.byref(x) for x in v]), "ligand_info")
+        self.n_atoms, self.n_torsions, self.n_genes, self.n_pairs, self.n_fragments = (x.value for x in v)
+
+    def free(self):
+        if self.h is not None and self.ctx.h is not None:
+            self.ctx.lib.free_ligand(self.ctx.h, self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def load_ligand(ctx: Context, xyz, types, charges, bonds, rotatable) -> Ligand:
+    x = np.ascontiguousarray(xyz, dtype=np.float64)
+    t = np.ascontiguousarray(types, dtype=np.int32)
+    q = np.ascontiguousarray(charges, dtype=np.float64)
+    b = np.ascontiguousarray(bonds, dtype=np.int32).reshape(-1, 2)
+    r = np.ascontiguousarray(rotatable, dtype=np.int32)
+    h = C.c_void_p()
+    ctx.check(ctx.lib.load_ligand(ctx.h, len(t), _ptr(x), _ptr(t), _ptr(q), len(r), _ptr(b), _ptr(r), C.byref(h)),
+              "load_ligand")
+    return Ligand(ctx, h)
+
+
+def score_batch(ctx: Context, grids: Grids, lig: Ligand, geno: torch.Tensor, E: torch.Tensor | None = None,
+                stream=None) -> torch.Tensor:
+    B = geno.shape[0]
+    if E is None:
+        E = torch.empty(B, dtype=torch.float32, device=geno.device)
+    ctx.check(ctx.lib.score_batch(ctx.h, grids.h, lig.h, _ptr(geno), B, _ptr(E), _stream(stream)), "score_batch")
+    return E
+
+
+def score_grad_batch(ctx: Context, grids: Grids, lig: Ligand, geno: torch.Tensor, E: torch.Tensor | None = None,
+                     grad: torch.Tensor | None = None, stream=None):
+    B = geno.shape[0]
+    if E is None:
+        E = torch.empty(B, dtype=torch.float32, device=geno.device)
+    if grad is None:
+        grad = torch.empty_like(geno)
+    ctx.check(ctx.lib.score_grad_batch(ctx.h, grids.h, lig.h, _ptr(geno), B, _ptr(E), _ptr(grad), _stream(stream)),
+              "score_grad_batch")
+    return E, grad
+
+
+def pose_batch(ctx: Context, lig: Ligand, geno: torch.Tensor, stream=None) -> torch.Tensor:
+    B = geno.shape[0]
+    xyz = torch.empty((B, lig.n_atoms, 3), dtype=torch.float32, device=geno.device)
+    ctx.check(ctx.lib.pose_batch(ctx.h, lig.h, _ptr(geno), B, _ptr(xyz), _stream(stream)), "pose_batch")
+    return xyz
+
+
+def dock(ctx: Context, grids: Grids, lig: Ligand, params: DockParams, seed: int):
+    """Blocking form with host outputs: (best_geno [R,G] f32, best_E [R] f64, evals [R] i64)."""
+    R, G = params.nruns, lig.n_genes
+    bg = np.zeros((R, G), dtype=np.float32)
+    be = np.zeros(R, dtype=np.float64)
+    ev = np.zeros(R, dtype=np.int64)
+    ctx.check(ctx.lib.dock(ctx.h, grids.h, lig.h, C.byref(params), int(seed), _ptr(bg), _ptr(be), _ptr(ev)), "dock")
+    return bg, be, ev
+
+
+def dock_async(ctx: Context, grids: Grids, lig: Ligand, params: DockParams, seed: int, out=None, stream=None):
+    """Queued form with device outputs: dict of tensors best_geno, best_E32, best_E, evals."""
+    R, G = params.nruns, lig.n_genes
+    dev = torch.device("cuda", ctx.device)
+    if out is None:
+        out = dict(best_geno=torch.empty((R, G), dtype=torch.float32, device=dev),
+                   best_E32=torch.empty(R, dtype=torch.float32, device=dev),
+                   best_E=torch.empty(R, dtype=torch.float64, device=dev),
+                   evals=torch.empty(R, dtype=torch.int64, device=dev))
+    ctx.check(ctx.lib.dock_async(ctx.h, grids.h, lig.h, C.byref(params), int(seed), _ptr(out["best_geno"]),
+                                 _ptr(out["best_E32"]), _ptr(out["best_E"]), _ptr(out["evals"]), _stream(stream)),
+              "dock_async")
+    return out
+
+
+def dock_init_population(ctx, grids, n_torsions, pop, nruns, seed, stream=None):
+    out = torch.empty((nruns, pop, 7 + n_torsions), dtype=torch.float32, device=f"cuda:{ctx.device}")
+    ctx.check(ctx.lib.dock_init_population(ctx.h, grids.h, n_torsions, pop, nruns, int(seed), _ptr(out),
+                                           _stream(stream)), "dock_init_population")
+    return out
+
+
+def dock_ga_children(ctx, n_torsions, pop_old: torch.Tensor, E_old: torch.Tensor, seed, generation,
+                     params: DockParams | None = None, with_info=True, stream=None):
+    nruns, pop, _ = pop_old.shape
+    new = torch.empty_like(pop_old)
+    info = torch.empty((nruns, pop, 5), dtype=torch.int64, device=pop_old.device) if with_info else None
+    ctx.check(ctx.lib.dock_ga_children(ctx.h, n_torsions, pop, nruns, _ptr(pop_old), _ptr(E_old), int(seed),
+                                       int(generation), C.byref(params) if params is not None else None, _ptr(new),
+                                       _ptr(info), _stream(stream)), "dock_ga_children")
+    return new, info
+
+
+def dock_ls_picks(ctx, pop, n_ls, nruns, seed, generation, stream=None):
+    out = torch.empty((nruns, max(n_ls, 1)), dtype=torch.int32, device=f"cuda:{ctx.device}")
+    ctx.check(ctx.lib.dock_ls_picks(ctx.h, pop, n_ls, nruns, int(seed), int(generation), _ptr(out), _stream(stream)),
+              "dock_ls_picks")
+    return out[:, :n_ls]
+
+
+def dock_local_search(ctx, grids, lig, x0: torch.Tensor, iters: int, rho=0.8, eps=1e-2, stream=None):
+    B = x0.shape[0]
+    xb = torch.empty_like(x0)
+    Eb = torch.empty(B, dtype=torch.float32, device=x0.device)
+    ctx.check(ctx.lib.dock_local_search(ctx.h, grids.h, lig.h, _ptr(x0), B, int(iters), float(rho), float(eps),
+                                        _ptr(xb), _ptr(Eb), _stream(stream)), "dock_local_search")
+    return xb, Eb
+
+
+def dock_philox(ctx, ctr: torch.Tensor, key_lo: int, key_hi: int, stream=None) -> torch.Tensor:
+    n = ctr.shape[0]
+    out = torch.empty((n, 4), dtype=torch.int32, device=ctr.device)
+    ctx.check(ctx.lib.dock_philox(ctx.h, _ptr(ctr), n, key_lo, key_hi, _ptr(out), _stream(stream)), "dock_philox")
+    return out
+
+
+# ---------------------------------------------------------------------------
+# convenience: objects from the seeded synthetic inputs
+
+def ligand_from(ctx: Context, lig) -> Ligand:
+    return load_ligand(ctx, lig.xyz, lig.types, lig.charges, lig.bonds, lig.rotatable)
+
+
+def grids_from_maps(ctx: Context, maps: np.ndarray, box) -> Grids:
+    mt = list(box.map_types) + [MAP_ELEC, MAP_DESOLV]
+    return load_grids(ctx, maps, box.dims, box.origin, box.spacing, mt)
+
+
+def grids_from_receptor(ctx: Context, rec, box) -> Grids:
+    return build_grids(ctx, rec.xyz, rec.types, rec.charges, box.dims, box.origin, box.spacing, box.map_types)

@@ -1,0 +1,673 @@
+// host.cpp -- context, memory, errors, tracing, ligand preprocessing and
+// grid loading of libdock.so.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <queue>
+#include <string>
+#include <vector>
+
+#include "forcefield.h"
+#include "internal.h"
+
+// ---------------------------------------------------------------------------
+// errors, memory, tracing
+
+int set_err(dock_ctx *ctx, int code, const std::string &msg) {
+    if (ctx) ctx->err = msg;
+    return code;
+}
+
+int cuda_err(dock_ctx *ctx, cudaError_t e, const char *what) {
+    return set_err(ctx, e == cudaErrorMemoryAllocation ? DOCK_ERR_OOM : DOCK_ERR_CUDA,
+                   std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+void *dev_alloc(dock_ctx *ctx, size_t bytes, cudaStream_t s) {
+    if (bytes == 0) bytes = 16;
+    if (ctx->has_alloc) return ctx->alloc.alloc(bytes, (void *)s, ctx->alloc.user);
+    void *p = nullptr;
+    if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void dev_free(dock_ctx *ctx, void *p, cudaStream_t s) {
+    if (!p) return;
+    if (ctx->has_alloc) ctx->alloc.free(p, (void *)s, ctx->alloc.user);
+    else cudaFreeAsync(p, s);
+}
+
+int kernel_id(dock_ctx *ctx, const char *name) {
+    for (size_t i = 0; i < ctx->kernel_names.size(); ++i)
+        if (ctx->kernel_names[i] == name) return (int)i;
+    ctx->kernel_names.emplace_back(name);
+    ctx->kernel_ms.push_back(0.0);
+    ctx->kernel_launches.push_back(0);
+    return (int)ctx->kernel_names.size() - 1;
+}
+
+static cudaEvent_t pool_event(dock_ctx *ctx) {
+    if (!ctx->event_pool.empty()) {
+        cudaEvent_t e = ctx->event_pool.back();
+        ctx->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void timing_begin(dock_ctx *ctx, int kid, cudaStream_t s, TimedLaunch *tl) {
+    tl->kernel = -1;
+    if (!ctx->timing) return;
+    tl->kernel = kid;
+    tl->start = pool_event(ctx);
+    tl->stop = pool_event(ctx);
+    cudaEventRecord(tl->start, s);
+}
+
+void timing_end(dock_ctx *ctx, cudaStream_t s, TimedLaunch *tl) {
+    if (tl->kernel < 0) return;
+    cudaEventRecord(tl->stop, s);
+    ctx->pending.push_back(*tl);
+}
+
+static void flush_timing(dock_ctx *ctx, bool keep) {
+    for (const TimedLaunch &t : ctx->pending) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(t.stop) == cudaSuccess && cudaEventElapsedTime(&ms, t.start, t.stop) == cudaSuccess &&
+            keep) {
+            ctx->kernel_ms[t.kernel] += ms;
+            ctx->kernel_launches[t.kernel] += 1;
+        }
+        ctx->event_pool.push_back(t.start);
+        ctx->event_pool.push_back(t.stop);
+    }
+    ctx->pending.clear();
+}
+
+int check_maps(dock_ctx *ctx, const dock_grids *g, const dock_ligand *l) {
+    for (int t : l->types)
+        if (g->map_of_type[t] < 0) return set_err(ctx, DOCK_ERR_NOMAP, "ligand atom type without a map");
+    return DOCK_OK;
+}
+
+extern "C" {
+
+int dock_version(void) { return 100; }
+
+void dock_default_params(dock_params *p) {
+    if (!p) return;
+    p->pop_size = 150;
+    p->nruns = 10;
+    p->max_evals = 100000;
+    p->ls_count = -1;
+    p->ls_iters = 100;
+    p->rho = 0.8f;
+    p->eps = 1e-2f;
+    p->p_tour = 0.6f;
+    p->p_cross = 0.8f;
+    p->p_mut = 0.02f;
+    p->trans_mut = 2.0f;
+}
+
+int dock_create(dock_ctx **out, int device, const dock_allocator *alloc) {
+    if (!out) return DOCK_ERR_INVALID;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+        cudaGetLastError();
+        return DOCK_ERR_CUDA;
+    }
+    if (cudaSetDevice(device) != cudaSuccess) return DOCK_ERR_CUDA;
+    dock_ctx *c = new dock_ctx();
+    c->device = device;
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    c->smem_optin = (size_t)optin;
+    if (alloc && alloc->alloc && alloc->free) {
+        c->alloc = *alloc;
+        c->has_alloc = true;
+    }
+    *out = c;
+    return DOCK_OK;
+}
+
+int dock_destroy(dock_ctx *ctx) {
+    if (!ctx) return DOCK_ERR_INVALID;
+    flush_timing(ctx, false);
+    for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
+    delete ctx;
+    return DOCK_OK;
+}
+
+const char *dock_last_error(const dock_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int dock_set_timing(dock_ctx *ctx, int enable) {
+    if (!ctx) return DOCK_ERR_INVALID;
+    ctx->timing = enable != 0;
+    return DOCK_OK;
+}
+
+int dock_reset_timing(dock_ctx *ctx) {
+    if (!ctx) return DOCK_ERR_INVALID;
+    flush_timing(ctx, false);
+    std::fill(ctx->kernel_ms.begin(), ctx->kernel_ms.end(), 0.0);
+    std::fill(ctx->kernel_launches.begin(), ctx->kernel_launches.end(), 0);
+    return DOCK_OK;
+}
+
+int dock_kernel_time(dock_ctx *ctx, const char *kernel, double *total_ms, int64_t *launches) {
+    if (!ctx || !kernel) return DOCK_ERR_INVALID;
+    flush_timing(ctx, true);
+    const int k = kernel_id(ctx, kernel);
+    if (total_ms) *total_ms = ctx->kernel_ms[k];
+    if (launches) *launches = ctx->kernel_launches[k];
+    return DOCK_OK;
+}
+
+int64_t dock_launch_count(const dock_ctx *ctx) { return ctx ? ctx->launches : -1; }
+
+// ---------------------------------------------------------------------------
+// grids
+
+static int finish_grids(dock_ctx *ctx, dock_grids *g, const int dims[3], const double origin[3], double spacing,
+                        cudaStream_t s) {
+    GridDev &d = g->dev;
+    d.nx = dims[0];
+    d.ny = dims[1];
+    d.nz = dims[2];
+    d.M = g->n_maps;
+    d.ox = (float)origin[0];
+    d.oy = (float)origin[1];
+    d.oz = (float)origin[2];
+    d.h = (float)spacing;
+    d.inv_h = (float)(1.0 / spacing);
+    d.ox64 = origin[0];
+    d.oy64 = origin[1];
+    d.oz64 = origin[2];
+    d.h64 = spacing;
+    for (int a = 0; a < 3; ++a) {
+        d.box_lo[a] = (float)origin[a];
+        d.box_len[a] = (float)((dims[a] - 1) * spacing);
+    }
+    d.emap = d.dmap = -1;
+    for (int m = 0; m < g->n_maps; ++m) {
+        const int t = g->map_type[m];
+        if (t == DOCK_MAP_ELEC) d.emap = m;
+        else if (t == DOCK_MAP_DESOLV) d.dmap = m;
+        else g->map_of_type[t] = m;
+    }
+    const size_t ncell = (size_t)(d.nx - 1) * (d.ny - 1) * (d.nz - 1);
+    g->cells_mem = dev_alloc(ctx, ncell * d.M * 32, s);
+    g->lut_mem = dev_alloc(ctx, 8 * sizeof(int), s);
+    if (!g->cells_mem || !g->lut_mem) return set_err(ctx, DOCK_ERR_OOM, "grid allocation failed");
+    d.cells = (const float4 *)g->cells_mem;
+    d.map_of_type = (const int *)g->lut_mem;
+    cudaError_t e = cudaMemcpyAsync(g->lut_mem, g->map_of_type, 8 * sizeof(int), cudaMemcpyHostToDevice, s);
+    if (!e) e = launch_relayout(d, (float4 *)g->cells_mem, s);
+    if (!e) e = cudaStreamSynchronize(s);
+    if (e) return cuda_err(ctx, e, "grid upload");
+    return DOCK_OK;
+}
+
+static int check_box(dock_ctx *ctx, const int dims[3], const double origin[3], double spacing) {
+    if (!dims || !origin) return set_err(ctx, DOCK_ERR_INVALID, "null grid geometry");
+    for (int a = 0; a < 3; ++a)
+        if (dims[a] < 2 || dims[a] > 4096 || !isfinite(origin[a]))
+            return set_err(ctx, DOCK_ERR_INVALID, "grid dims must be in 2..4096 and the origin finite");
+    if (!(spacing > 0.0) || !isfinite(spacing)) return set_err(ctx, DOCK_ERR_INVALID, "spacing must be > 0");
+    return DOCK_OK;
+}
+
+int load_grids(dock_ctx *ctx, const float *maps, int n_maps, const int dims[3], const double origin[3], double spacing,
+               const int *map_type, dock_grids **out) {
+    if (!ctx || !out) return DOCK_ERR_INVALID;
+    *out = nullptr;
+    int rc = check_box(ctx, dims, origin, spacing);
+    if (rc) return rc;
+    if (!maps || !map_type || n_maps < 3 || n_maps > DOCK_NTYPES + 2)
+        return set_err(ctx, DOCK_ERR_INVALID, "need 3..9 maps");
+    int ne = 0, nd = 0, seen[DOCK_NTYPES] = {0};
+    for (int m = 0; m < n_maps; ++m) {
+        const int t = map_type[m];
+        if (t == DOCK_MAP_ELEC) ++ne;
+        else if (t == DOCK_MAP_DESOLV) ++nd;
+        else if (t < 0 || t >= DOCK_NTYPES || seen[t]++) return set_err(ctx, DOCK_ERR_INVALID, "bad or repeated map type");
+    }
+    if (ne != 1 || nd != 1) return set_err(ctx, DOCK_ERR_INVALID, "need exactly one electrostatic and one desolvation map");
+    const size_t nn = (size_t)dims[0] * dims[1] * dims[2];
+    for (size_t i = 0; i < nn * n_maps; ++i)
+        if (!isfinite(maps[i])) return set_err(ctx, DOCK_ERR_INVALID, "non-finite map value");
+    dock_grids *g = new dock_grids();
+    g->n_maps = n_maps;
+    g->map_type.assign(map_type, map_type + n_maps);
+    cudaStream_t s = nullptr;
+    g->nodes_mem = dev_alloc(ctx, nn * n_maps * 4, s);
+    if (!g->nodes_mem) {
+        free_grids(ctx, g);
+        return set_err(ctx, DOCK_ERR_OOM, "grid allocation failed");
+    }
+    g->dev.nodes = (const float *)g->nodes_mem;
+    cudaError_t e = cudaMemcpyAsync(g->nodes_mem, maps, nn * n_maps * 4, cudaMemcpyHostToDevice, s);
+    if (e) {
+        free_grids(ctx, g);
+        return cuda_err(ctx, e, "grid upload");
+    }
+    rc = finish_grids(ctx, g, dims, origin, spacing, s);
+    if (rc) {
+        free_grids(ctx, g);
+        return rc;
+    }
+    *out = g;
+    return DOCK_OK;
+}
+
+int build_grids(dock_ctx *ctx, int n_rec, const double *rxyz, const int *rtype, const double *rq, const int dims[3],
+                const double origin[3], double spacing, int n_type_maps, const int *map_types, dock_grids **out) {
+    if (!ctx || !out) return DOCK_ERR_INVALID;
+    *out = nullptr;
+    int rc = check_box(ctx, dims, origin, spacing);
+    if (rc) return rc;
+    if (n_rec < 1 || !rxyz || !rtype || !rq || n_type_maps < 1 || n_type_maps > DOCK_NTYPES || !map_types)
+        return set_err(ctx, DOCK_ERR_INVALID, "bad receptor or map list");
+    int seen[DOCK_NTYPES] = {0};
+    for (int m = 0; m < n_type_maps; ++m)
+        if (map_types[m] < 0 || map_types[m] >= DOCK_NTYPES || seen[map_types[m]]++)
+            return set_err(ctx, DOCK_ERR_INVALID, "bad or repeated map type");
+    std::vector<float4> rec(n_rec);
+    for (int j = 0; j < n_rec; ++j) {
+        if (rtype[j] < 0 || rtype[j] >= DOCK_NTYPES) return set_err(ctx, DOCK_ERR_TYPE, "unknown receptor atom type");
+        rec[j] = make_float4((float)(rxyz[3 * j] - origin[0]), (float)(rxyz[3 * j + 1] - origin[1]),
+                             (float)(rxyz[3 * j + 2] - origin[2]), (float)rq[j]);
+    }
+    dock_grids *g = new dock_grids();
+    g->n_maps = n_type_maps + 2;
+    g->map_type.assign(map_types, map_types + n_type_maps);
+    g->map_type.push_back(DOCK_MAP_ELEC);
+    g->map_type.push_back(DOCK_MAP_DESOLV);
+    cudaStream_t s = nullptr;
+    const size_t nn = (size_t)dims[0] * dims[1] * dims[2];
+    g->nodes_mem = dev_alloc(ctx, nn * g->n_maps * 4, s);
+    float4 *drec = (float4 *)dev_alloc(ctx, n_rec * sizeof(float4), s);
+    int *dt = (int *)dev_alloc(ctx, n_rec * sizeof(int), s);
+    cudaError_t e = cudaSuccess;
+    if (!g->nodes_mem || !drec || !dt) {
+        rc = set_err(ctx, DOCK_ERR_OOM, "grid allocation failed");
+    } else {
+        g->dev.nodes = (const float *)g->nodes_mem;
+        e = cudaMemcpyAsync(drec, rec.data(), n_rec * sizeof(float4), cudaMemcpyHostToDevice, s);
+        if (!e) e = cudaMemcpyAsync(dt, rtype, n_rec * sizeof(int), cudaMemcpyHostToDevice, s);
+        if (!e) e = launch_build_maps(n_rec, drec, dt, dims[0], dims[1], dims[2], spacing, n_type_maps, map_types,
+                                      (float *)g->nodes_mem, s);
+        if (!e) ++ctx->launches;
+        if (!e) e = cudaStreamSynchronize(s);
+        if (e) rc = cuda_err(ctx, e, "map builder");
+    }
+    dev_free(ctx, drec, s);
+    dev_free(ctx, dt, s);
+    if (!rc) rc = finish_grids(ctx, g, dims, origin, spacing, s);
+    if (rc) {
+        free_grids(ctx, g);
+        return rc;
+    }
+    *out = g;
+    return DOCK_OK;
+}
+
+int grids_read_maps(dock_ctx *ctx, const dock_grids *g, float *maps_out) {
+    if (!ctx || !g || !maps_out) return DOCK_ERR_INVALID;
+    const size_t n = (size_t)g->dev.nx * g->dev.ny * g->dev.nz * g->n_maps;
+    cudaError_t e = cudaMemcpy(maps_out, g->nodes_mem, n * 4, cudaMemcpyDeviceToHost);
+    return e ? cuda_err(ctx, e, "grid download") : DOCK_OK;
+}
+
+int free_grids(dock_ctx *ctx, dock_grids *g) {
+    if (!ctx || !g) return DOCK_ERR_INVALID;
+    cudaStreamSynchronize(nullptr);
+    dev_free(ctx, g->cells_mem, nullptr);
+    dev_free(ctx, g->nodes_mem, nullptr);
+    dev_free(ctx, g->lut_mem, nullptr);
+    delete g;
+    return DOCK_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// ligand preprocessing
+
+namespace {
+
+struct Blob {
+    std::vector<unsigned char> bytes;
+    size_t add(const void *p, size_t n) {
+        size_t off = (bytes.size() + 15) & ~(size_t)15;
+        bytes.resize(off + (n ? n : 16));
+        if (n) memcpy(bytes.data() + off, p, n);
+        return off;
+    }
+};
+
+}  // namespace
+
+extern "C" int load_ligand(dock_ctx *ctx, int n, const double *xyz, const int *type, const double *charge, int nb,
+                           const int *bonds, const int *rot, dock_ligand **out) {
+    if (!ctx || !out) return DOCK_ERR_INVALID;
+    *out = nullptr;
+    if (n < 1 || n > DOCK_MAX_ATOMS) return set_err(ctx, DOCK_ERR_SIZE, "atom count must be 1..255");
+    if (!xyz || !type || !charge || nb < 0 || (nb > 0 && (!bonds || !rot)))
+        return set_err(ctx, DOCK_ERR_INVALID, "null ligand array");
+    for (int i = 0; i < n; ++i) {
+        if (type[i] < 0 || type[i] >= DOCK_NTYPES) return set_err(ctx, DOCK_ERR_TYPE, "unknown atom type");
+        if (!isfinite(xyz[3 * i]) || !isfinite(xyz[3 * i + 1]) || !isfinite(xyz[3 * i + 2]) || !isfinite(charge[i]))
+            return set_err(ctx, DOCK_ERR_INVALID, "non-finite coordinate or charge");
+    }
+    int nt = 0;
+    std::vector<std::vector<std::pair<int, int>>> adj(n);  // (neighbour, bond)
+    for (int b = 0; b < nb; ++b) {
+        const int u = bonds[2 * b], v = bonds[2 * b + 1];
+        if (u < 0 || v < 0 || u >= n || v >= n || u == v) return set_err(ctx, DOCK_ERR_INVALID, "bad bond");
+        adj[u].push_back({v, b});
+        adj[v].push_back({u, b});
+        nt += rot[b] ? 1 : 0;
+    }
+    if (nt > DOCK_MAX_TORSIONS) return set_err(ctx, DOCK_ERR_SIZE, "more than 32 rotatable bonds");
+    // flood fill from `start`, skipping bond `skip` (and rotatable bonds if rigid)
+    auto flood = [&](int start, int skip, bool rigid, std::vector<int> &lab, int id) {
+        std::vector<int> st{start};
+        lab[start] = id;
+        int cnt = 0;
+        while (!st.empty()) {
+            const int a = st.back();
+            st.pop_back();
+            ++cnt;
+            for (auto [w, b] : adj[a])
+                if (b != skip && !(rigid && rot[b]) && lab[w] < 0) {
+                    lab[w] = id;
+                    st.push_back(w);
+                }
+        }
+        return cnt;
+    };
+    std::vector<int> lab(n, -1);
+    if (flood(0, -1, false, lab, 0) != n) return set_err(ctx, DOCK_ERR_DISCONNECTED, "bond graph is not connected");
+    for (int b = 0; b < nb; ++b) {
+        if (!rot[b]) continue;
+        std::fill(lab.begin(), lab.end(), -1);
+        flood(bonds[2 * b], b, false, lab, 0);
+        if (lab[bonds[2 * b + 1]] >= 0) return set_err(ctx, DOCK_ERR_RING, "rotatable bond inside a ring");
+    }
+    // rigid fragments, numbered by their lowest atom
+    std::vector<int> comp(n, -1), fsize;
+    for (int i = 0; i < n; ++i)
+        if (comp[i] < 0) fsize.push_back(flood(i, -1, true, comp, (int)fsize.size()));
+    const int F = (int)fsize.size();
+    int root = 0;
+    for (int f = 1; f < F; ++f)
+        if (fsize[f] > fsize[root]) root = f;
+    // torsion tree: depth-first preorder of fragments from the root; children
+    // in the order of their entering bond in the input
+    std::vector<int> rank(nb, -1);
+    for (int b = 0, k = 0; b < nb; ++b)
+        if (rot[b]) rank[b] = k++;
+    std::vector<std::vector<std::pair<int, int>>> fadj(F);  // (fragment, bond)
+    for (int b = 0; b < nb; ++b)
+        if (rot[b]) {
+            fadj[comp[bonds[2 * b]]].push_back({comp[bonds[2 * b + 1]], b});
+            fadj[comp[bonds[2 * b + 1]]].push_back({comp[bonds[2 * b]], b});
+        }
+    std::vector<int> order, fparent(F, -1), fbond(F, -1), newf(F, -1);
+    {
+        std::vector<std::pair<int, int>> st{{root, -1}};
+        std::vector<char> vis(F, 0);
+        while (!st.empty()) {
+            auto [f, via] = st.back();
+            st.pop_back();
+            if (vis[f]) continue;
+            vis[f] = 1;
+            fbond[f] = via;
+            newf[f] = (int)order.size();
+            order.push_back(f);
+            std::vector<std::pair<int, int>> kids;
+            for (auto [g, b] : fadj[f])
+                if (!vis[g]) kids.push_back({b, g});
+            std::sort(kids.begin(), kids.end());
+            for (auto it = kids.rbegin(); it != kids.rend(); ++it) {
+                fparent[it->second] = f;
+                st.push_back({it->second, it->first});
+            }
+        }
+    }
+    if ((int)order.size() != F) return set_err(ctx, DOCK_ERR_DISCONNECTED, "torsion tree is not connected");
+    std::vector<int> depth(F, 0), sub_end(F, 0);
+    for (int k = 1; k < F; ++k) depth[k] = depth[newf[fparent[order[k]]]] + 1;
+    for (int k = F - 1; k >= 0; --k) {
+        int e = k + 1;
+        for (int j = k + 1; j < F && depth[j] > depth[k]; ++j) e = j + 1;
+        sub_end[k] = e;
+    }
+    // atoms: fragment by fragment in preorder, ascending input index inside
+    std::vector<int> perm, inv(n, -1);
+    std::vector<int4> frag(F);
+    for (int k = 0; k < F; ++k) {
+        const int f = order[k], begin = (int)perm.size();
+        for (int i = 0; i < n; ++i)
+            if (comp[i] == f) {
+                inv[i] = (int)perm.size();
+                perm.push_back(i);
+            }
+        frag[k] = make_int4(begin, (int)perm.size(), k ? newf[fparent[f]] : -1, depth[k]);
+    }
+    double c[3] = {0, 0, 0};
+    for (int i = 0; i < n; ++i)
+        for (int a = 0; a < 3; ++a) c[a] += xyz[3 * i + a];
+    for (int a = 0; a < 3; ++a) c[a] /= n;
+    std::vector<double> ref64(3 * n), q64(n);
+    std::vector<float4> ref(n);
+    std::vector<int> meta(n), types(n);
+    for (int k = 0; k < n; ++k) {
+        const int i = perm[k];
+        for (int a = 0; a < 3; ++a) ref64[3 * k + a] = xyz[3 * i + a] - c[a];
+        q64[k] = charge[i];
+        ref[k] = make_float4((float)ref64[3 * k], (float)ref64[3 * k + 1], (float)ref64[3 * k + 2], (float)charge[i]);
+        meta[k] = type[i] | (comp[i] >= 0 ? newf[comp[i]] << 8 : 0);
+        types[k] = type[i];
+    }
+    const int T = F - 1;
+    std::vector<float4> tu(std::max(T, 1)), tb(std::max(T, 1));
+    std::vector<int2> tab(std::max(T, 1));
+    std::vector<int> tgene(std::max(T, 1)), fdepth_max(1, 0);
+    int max_depth = 0;
+    for (int k = 0; k < T; ++k) {
+        const int f = order[k + 1], b = fbond[f];
+        int ua = bonds[2 * b], ub = bonds[2 * b + 1];
+        if (comp[ub] != f) std::swap(ua, ub);  // ub on the child (moving) side
+        const int ia = inv[ua], ib = inv[ub];
+        double u[3] = {ref64[3 * ib] - ref64[3 * ia], ref64[3 * ib + 1] - ref64[3 * ia + 1],
+                       ref64[3 * ib + 2] - ref64[3 * ia + 2]};
+        const double len = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+        if (!(len > 0)) return set_err(ctx, DOCK_ERR_INVALID, "zero-length rotatable bond");
+        tu[k] = make_float4((float)(u[0] / len), (float)(u[1] / len), (float)(u[2] / len), 0.f);
+        tb[k] = make_float4((float)ref64[3 * ib], (float)ref64[3 * ib + 1], (float)ref64[3 * ib + 2], 0.f);
+        tab[k] = make_int2(ia, ib);
+        tgene[k] = 7 + rank[b];
+        max_depth = std::max(max_depth, depth[k + 1]);
+    }
+    // bond-graph distances (input numbering)
+    std::vector<int> dist((size_t)n * n, -1);
+    for (int s0 = 0; s0 < n; ++s0) {
+        int *d = dist.data() + (size_t)s0 * n;
+        std::queue<int> q;
+        d[s0] = 0;
+        q.push(s0);
+        while (!q.empty()) {
+            const int a = q.front();
+            q.pop();
+            for (auto [w, b] : adj[a])
+                if (d[w] < 0) {
+                    d[w] = d[a] + 1;
+                    q.push(w);
+                }
+        }
+    }
+    // pair list: different rigid fragments, >= 4 bonds apart
+    std::vector<uint32_t> pij;
+    std::vector<float4> pc;
+    std::vector<float> pds;
+    std::vector<double> pc64;
+    for (int i = 0; i < n; ++i)
+        for (int j = i + 1; j < n; ++j) {
+            const int I = perm[i], J = perm[j];
+            if (comp[I] == comp[J] || dist[(size_t)I * n + J] < 4) continue;
+            double c12, c6, c10;
+            ff::vdw_coefs(type[I], type[J], c12, c6, c10);
+            const double qq = ff::kWel * ff::kCoulomb * charge[I] * charge[J];
+            const double ds = ff::kWds * (ff::solv(type[I], charge[I]) * ff::kTypes[type[J]].vol +
+                                          ff::solv(type[J], charge[J]) * ff::kTypes[type[I]].vol);
+            pij.push_back((uint32_t)i | ((uint32_t)j << 16));
+            pc.push_back(make_float4((float)c12, (float)c6, (float)c10, (float)qq));
+            pds.push_back((float)ds);
+            pc64.insert(pc64.end(), {c12, c6, c10, qq, ds});
+        }
+    const int P = (int)pij.size();
+    std::vector<std::vector<uint32_t>> lists(n);
+    for (int p = 0; p < P; ++p) {
+        const int i = pij[p] & 0xffff, j = pij[p] >> 16;
+        lists[i].push_back((uint32_t)p | ((uint32_t)j << 16));
+        lists[j].push_back((uint32_t)p | ((uint32_t)i << 16));
+    }
+    std::vector<int> adj_off(n + 1, 0);
+    std::vector<uint32_t> adjv;
+    for (int i = 0; i < n; ++i) {
+        adj_off[i] = (int)adjv.size();
+        adjv.insert(adjv.end(), lists[i].begin(), lists[i].end());
+    }
+    adj_off[n] = (int)adjv.size();
+
+    Blob B;
+    const size_t o_ref = B.add(ref.data(), n * sizeof(float4));
+    const size_t o_meta = B.add(meta.data(), n * sizeof(int));
+    const size_t o_perm = B.add(perm.data(), n * sizeof(int));
+    const size_t o_frag = B.add(frag.data(), F * sizeof(int4));
+    const size_t o_sub = B.add(sub_end.data(), F * sizeof(int));
+    const size_t o_tu = B.add(tu.data(), T * sizeof(float4));
+    const size_t o_tb = B.add(tb.data(), T * sizeof(float4));
+    const size_t o_tab = B.add(tab.data(), T * sizeof(int2));
+    const size_t o_tg = B.add(tgene.data(), T * sizeof(int));
+    const size_t o_pij = B.add(pij.data(), P * sizeof(uint32_t));
+    const size_t o_pc = B.add(pc.data(), P * sizeof(float4));
+    const size_t o_pds = B.add(pds.data(), P * sizeof(float));
+    const size_t o_aoff = B.add(adj_off.data(), (n + 1) * sizeof(int));
+    const size_t o_adj = B.add(adjv.data(), adjv.size() * sizeof(uint32_t));
+    const size_t o_r64 = B.add(ref64.data(), 3 * n * sizeof(double));
+    const size_t o_pc64 = B.add(pc64.data(), pc64.size() * sizeof(double));
+    const size_t o_q64 = B.add(q64.data(), n * sizeof(double));
+
+    dock_ligand *L = new dock_ligand();
+    L->blob_bytes = B.bytes.size();
+    L->blob = dev_alloc(ctx, L->blob_bytes, nullptr);
+    if (!L->blob) {
+        delete L;
+        return set_err(ctx, DOCK_ERR_OOM, "ligand allocation failed");
+    }
+    cudaError_t e = cudaMemcpyAsync(L->blob, B.bytes.data(), L->blob_bytes, cudaMemcpyHostToDevice, nullptr);
+    if (!e) e = cudaStreamSynchronize(nullptr);
+    if (e) {
+        dev_free(ctx, L->blob, nullptr);
+        delete L;
+        return cuda_err(ctx, e, "ligand upload");
+    }
+    const unsigned char *base = (const unsigned char *)L->blob;
+    LigandDev &d = L->dev;
+    d.n_atoms = n;
+    d.n_tors = T;
+    d.n_frag = F;
+    d.n_pairs = P;
+    d.n_genes = 7 + T;
+    d.max_depth = max_depth;
+    d.ref = (const float4 *)(base + o_ref);
+    d.meta = (const int *)(base + o_meta);
+    d.perm = (const int *)(base + o_perm);
+    d.frag = (const int4 *)(base + o_frag);
+    d.sub_end = (const int *)(base + o_sub);
+    d.tors_u = (const float4 *)(base + o_tu);
+    d.tors_b = (const float4 *)(base + o_tb);
+    d.tors_ab = (const int2 *)(base + o_tab);
+    d.tors_gene = (const int *)(base + o_tg);
+    d.pair_ij = (const uint32_t *)(base + o_pij);
+    d.pair_c = (const float4 *)(base + o_pc);
+    d.pair_ds = (const float *)(base + o_pds);
+    d.adj_off = (const int *)(base + o_aoff);
+    d.adj = (const uint32_t *)(base + o_adj);
+    d.ref64 = (const double *)(base + o_r64);
+    d.pair_c64 = (const double *)(base + o_pc64);
+    d.q64 = (const double *)(base + o_q64);
+    L->types = types;
+    *out = L;
+    return DOCK_OK;
+}
+
+extern "C" {
+
+int ligand_info(const dock_ligand *l, int *n_atoms, int *n_torsions, int *n_genes, int *n_pairs, int *n_fragments) {
+    if (!l) return DOCK_ERR_INVALID;
+    if (n_atoms) *n_atoms = l->dev.n_atoms;
+    if (n_torsions) *n_torsions = l->dev.n_tors;
+    if (n_genes) *n_genes = l->dev.n_genes;
+    if (n_pairs) *n_pairs = l->dev.n_pairs;
+    if (n_fragments) *n_fragments = l->dev.n_frag;
+    return DOCK_OK;
+}
+
+int free_ligand(dock_ctx *ctx, dock_ligand *l) {
+    if (!ctx || !l) return DOCK_ERR_INVALID;
+    cudaStreamSynchronize(nullptr);
+    dev_free(ctx, l->blob, nullptr);
+    delete l;
+    return DOCK_OK;
+}
+
+// ---------------------------------------------------------------------------
+// batched evaluation
+
+static int score_common(dock_ctx *ctx, const dock_grids *g, const dock_ligand *l, const float *geno, int B, float *E,
+                        float *grad, void *stream) {
+    if (!ctx) return DOCK_ERR_INVALID;
+    if (!g || !l || B < 0 || (B > 0 && (!geno || !E))) return set_err(ctx, DOCK_ERR_INVALID, "invalid argument");
+    int rc = check_maps(ctx, g, l);
+    if (rc) return rc;
+    if (B == 0) return DOCK_OK;
+    const WarpLayout W = warp_layout(l->dev.n_atoms, l->dev.n_frag, l->dev.n_pairs, grad != nullptr);
+    if (!evaluator_smem_ok(ctx, W, 1)) return set_err(ctx, DOCK_ERR_SIZE, "ligand too large for shared memory");
+    cudaError_t e = launch_score(ctx, l->dev, g->dev, geno, B, E, grad, (cudaStream_t)stream);
+    return e ? cuda_err(ctx, e, "score kernel") : DOCK_OK;
+}
+
+int score_batch(dock_ctx *ctx, const dock_grids *g, const dock_ligand *l, const float *geno, int B, float *E,
+                void *stream) {
+    return score_common(ctx, g, l, geno, B, E, nullptr, stream);
+}
+
+int score_grad_batch(dock_ctx *ctx, const dock_grids *g, const dock_ligand *l, const float *geno, int B, float *E,
+                     float *grad, void *stream) {
+    if (ctx && B > 0 && !grad) return set_err(ctx, DOCK_ERR_INVALID, "null gradient buffer");
+    return score_common(ctx, g, l, geno, B, E, grad, stream);
+}
+
+int pose_batch(dock_ctx *ctx, const dock_ligand *l, const float *geno, int B, float *xyz, void *stream) {
+    if (!ctx) return DOCK_ERR_INVALID;
+    if (!l || B < 0 || (B > 0 && (!geno || !xyz))) return set_err(ctx, DOCK_ERR_INVALID, "invalid argument");
+    if (B == 0) return DOCK_OK;
+    const WarpLayout W = warp_layout(l->dev.n_atoms, l->dev.n_frag, l->dev.n_pairs, false);
+    if (!evaluator_smem_ok(ctx, W, 1)) return set_err(ctx, DOCK_ERR_SIZE, "ligand too large for shared memory");
+    cudaError_t e = launch_pose(ctx, l->dev, geno, B, xyz, (cudaStream_t)stream);
+    return e ? cuda_err(ctx, e, "pose kernel") : DOCK_OK;
+}
+
+}  // extern "C"

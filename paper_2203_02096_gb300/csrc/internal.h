@@ -1,0 +1,136 @@
+// internal.h -- device data layouts and launch helpers of libdock.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "dock.h"
+
+#define DOCK_WARP 32
+
+// Ligand on the device.  Atoms are renumbered so that each rigid fragment is
+// a contiguous range and fragments follow a depth-first preorder of the
+// torsion tree (fragment 0 = root); then the atoms moved by the torsion
+// entering fragment f are exactly the fragments [f, sub_end[f]).  Internal
+// torsion k is the bond entering fragment k+1.
+struct LigandDev {
+    int n_atoms, n_tors, n_frag, n_pairs, n_genes, max_depth;
+    const float4 *ref;        // [n] centred reference coords, w = partial charge
+    const int *meta;          // [n] type | fragment << 8
+    const int *perm;          // [n] internal atom -> input atom
+    const int4 *frag;         // [F] (atom begin, atom end, parent, depth)
+    const int *sub_end;       // [F] end of the fragment's subtree (fragment numbering)
+    const float4 *tors_u;     // [T] unit bond axis a->b in the reference frame
+    const float4 *tors_b;     // [T] reference position of axis atom b
+    const int2 *tors_ab;      // [T] internal atom indices (a, b)
+    const int *tors_gene;     // [T] genotype index of internal torsion k
+    const uint32_t *pair_ij;  // [P] i | j << 16, internal atom indices
+    const float4 *pair_c;     // [P] (c12, c6, c10, w_el * 332.06 * q_i q_j)
+    const float *pair_ds;     // [P] w_ds (S_i V_j + S_j V_i)
+    const int *adj_off;       // [n+1] CSR over atoms of the pairs they take part in
+    const uint32_t *adj;      // [2P] pair index | partner atom << 16
+    const double *ref64;      // [n][3] centred reference coords (FP64 re-score)
+    const double *pair_c64;   // [P][5] c12, c6, c10, qq, ds (FP64 re-score)
+    const double *q64;        // [n] charges (FP64 re-score)
+};
+
+// Receptor grids on the device.  cells: cell-major copy, for cell
+// c = (iz*(ny-1) + iy)*(nx-1) + ix and map m the 8 corner values at
+// float4 index 2*(c*M + m): (v000, v100, v010, v110), (v001, v101, v011, v111)
+// (corner bits x, y, z), so one atom-map read is one 32-byte sector.
+struct GridDev {
+    const float4 *cells;
+    const float *nodes;       // [M][nz][ny][nx] node-major copy
+    const int *map_of_type;   // [8] ligand type -> map, -1 if absent
+    int nx, ny, nz, M;
+    float ox, oy, oz, h, inv_h;
+    int emap, dmap;
+    float box_lo[3], box_len[3];  // search box for initial translations (FP32, rounded once)
+    double ox64, oy64, oz64, h64;
+};
+
+// Per-warp shared-memory scratch of the evaluator, offsets in floats (each a
+// multiple of 4 so float4 views are aligned).
+struct WarpLayout {
+    int geno, grad, M, fs, x, f, s, total;
+};
+
+__host__ __device__ inline int round4(int v) { return (v + 3) & ~3; }
+
+__host__ __device__ inline WarpLayout warp_layout(int n_atoms, int n_frag, int n_pairs, bool grad) {
+    WarpLayout w;
+    int o = 0;
+    w.geno = o; o += 48;
+    w.grad = o; o += 48;
+    w.M = o; o += 12 * n_frag;
+    w.fs = o; o += grad ? 8 * n_frag : 0;
+    w.x = o; o += 4 * n_atoms;
+    w.f = o; o += grad ? 4 * n_atoms : 0;
+    w.s = o; o += grad ? round4(n_pairs) : 0;
+    w.total = round4(o);
+    return w;
+}
+
+// Library-side objects behind the opaque handles.
+struct TimedLaunch {
+    int kernel;
+    cudaEvent_t start, stop;
+};
+
+struct dock_ctx {
+    int device = 0;
+    int num_sms = 0;
+    size_t smem_optin = 0;
+    dock_allocator alloc{};
+    bool has_alloc = false;
+    std::string err;
+    bool timing = false;
+    std::vector<TimedLaunch> pending;
+    std::vector<cudaEvent_t> event_pool;
+    std::vector<std::string> kernel_names;
+    std::vector<double> kernel_ms;
+    std::vector<int64_t> kernel_launches;
+    int64_t launches = 0;
+    int *d_flag = nullptr;  // device error word: 0 = fine
+};
+
+struct dock_grids {
+    GridDev dev{};
+    int map_of_type[8] = {-1, -1, -1, -1, -1, -1, -1, -1};
+    void *cells_mem = nullptr;
+    void *nodes_mem = nullptr;
+    void *lut_mem = nullptr;
+    int n_maps = 0;
+    std::vector<int> map_type;
+};
+
+struct dock_ligand {
+    LigandDev dev{};
+    void *blob = nullptr;
+    size_t blob_bytes = 0;
+    std::vector<int> types;  // input types, for the map check
+};
+
+// ---- helpers shared by the library's translation units (host side) ----
+int set_err(dock_ctx *ctx, int code, const std::string &msg);
+int cuda_err(dock_ctx *ctx, cudaError_t e, const char *what);
+void *dev_alloc(dock_ctx *ctx, size_t bytes, cudaStream_t s);
+void dev_free(dock_ctx *ctx, void *p, cudaStream_t s);
+int kernel_id(dock_ctx *ctx, const char *name);
+void timing_begin(dock_ctx *ctx, int kid, cudaStream_t s, TimedLaunch *tl);
+void timing_end(dock_ctx *ctx, cudaStream_t s, TimedLaunch *tl);
+int check_maps(dock_ctx *ctx, const dock_grids *g, const dock_ligand *l);
+int evaluator_smem_ok(dock_ctx *ctx, const WarpLayout &w, int warps);
+
+// Kernel launchers (defined in the .cu files).
+cudaError_t launch_relayout(const GridDev &g, float4 *cells, cudaStream_t s);
+cudaError_t launch_build_maps(int n_rec, const float4 *rec_rel, const int *rtype, int nx, int ny, int nz, double h,
+                              int n_tmaps, const int *map_types, float *nodes, cudaStream_t s);
+cudaError_t launch_rescore64(dock_ctx *ctx, const LigandDev &L, const GridDev &G, const float *geno, int B, double *E,
+                             cudaStream_t s);
+cudaError_t launch_score(dock_ctx *ctx, const LigandDev &L, const GridDev &G, const float *geno, int B, float *E,
+                         float *grad, cudaStream_t s);
+cudaError_t launch_pose(dock_ctx *ctx, const LigandDev &L, const float *geno, int B, float *xyz, cudaStream_t s);

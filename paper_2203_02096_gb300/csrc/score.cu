@@ -1,0 +1,278 @@
+// score.cu -- batched energy / gradient / pose kernels, and the FP64
+// re-scoring of final poses.
+#include "eval.cuh"
+
+namespace {
+
+constexpr int kScoreWarps = 4;  // warps per block of the batched evaluators
+
+template <bool GRAD>
+__global__ void __launch_bounds__(kScoreWarps * 32)
+score_kernel(LigandDev L, GridDev G, const float *__restrict__ geno, int B, float *__restrict__ E,
+             float *__restrict__ grad, WarpLayout W) {
+    extern __shared__ float4 smem4[];
+    float *ws = reinterpret_cast<float *>(smem4) + (threadIdx.x >> 5) * W.total;
+    const int lane = threadIdx.x & 31;
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    const int Gn = L.n_genes;
+    for (int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); b < B; b += nw) {
+        const float *gb = geno + (size_t)b * Gn;
+        for (int j = lane; j < Gn; j += 32) ws[W.geno + j] = gb[j];
+        __syncwarp();
+        const float e = dev::eval_warp<GRAD>(L, G, ws, W, lane);
+        if (lane == 0) E[b] = e;
+        if (GRAD)
+            for (int j = lane; j < Gn; j += 32) grad[(size_t)b * Gn + j] = ws[W.grad + j];
+        __syncwarp();
+    }
+}
+
+// Pose only: the forward kinematics of the evaluator, written out per atom
+// in input order (x = t + d).
+__global__ void __launch_bounds__(kScoreWarps * 32)
+pose_kernel(LigandDev L, const float *__restrict__ geno, int B, float *__restrict__ xyz, WarpLayout W) {
+    extern __shared__ float4 smem4[];
+    float *ws = reinterpret_cast<float *>(smem4) + (threadIdx.x >> 5) * W.total;
+    const int lane = threadIdx.x & 31;
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    const int Gn = L.n_genes, T = L.n_tors;
+    float4 *M = reinterpret_cast<float4 *>(ws + W.M);
+    for (int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); b < B; b += nw) {
+        const float *g = geno + (size_t)b * Gn;
+        float qw = g[3], qx = g[4], qy = g[5], qz = g[6];
+        const float qn2 = qw * qw + qx * qx + qy * qy + qz * qz;
+        if (qn2 >= 1e-24f) {
+            const float qi = rsqrtf(qn2);
+            qw *= qi; qx *= qi; qy *= qi; qz *= qi;
+        } else {
+            qw = 1.f; qx = qy = qz = 0.f;
+        }
+        if (lane == 0) {
+            M[0] = make_float4(1.f - 2.f * (qy * qy + qz * qz), 2.f * (qx * qy - qw * qz), 2.f * (qx * qz + qw * qy), 0.f);
+            M[1] = make_float4(2.f * (qx * qy + qw * qz), 1.f - 2.f * (qx * qx + qz * qz), 2.f * (qy * qz - qw * qx), 0.f);
+            M[2] = make_float4(2.f * (qx * qz - qw * qy), 2.f * (qy * qz + qw * qx), 1.f - 2.f * (qx * qx + qy * qy), 0.f);
+        }
+        float r[9] = {0}, t[3] = {0};
+        int depth = 0, parent = 0;
+        if (lane < T) {
+            float s, c;
+            sincosf(g[__ldg(L.tors_gene + lane)], &s, &c);
+            const float4 u = __ldg(L.tors_u + lane), bb = __ldg(L.tors_b + lane);
+            const float oc = 1.f - c;
+            r[0] = fmaf(oc * u.x, u.x, c);        r[1] = fmaf(oc * u.x, u.y, -s * u.z); r[2] = fmaf(oc * u.x, u.z, s * u.y);
+            r[3] = fmaf(oc * u.y, u.x, s * u.z);  r[4] = fmaf(oc * u.y, u.y, c);        r[5] = fmaf(oc * u.y, u.z, -s * u.x);
+            r[6] = fmaf(oc * u.z, u.x, -s * u.y); r[7] = fmaf(oc * u.z, u.y, s * u.x);  r[8] = fmaf(oc * u.z, u.z, c);
+            t[0] = bb.x - (r[0] * bb.x + r[1] * bb.y + r[2] * bb.z);
+            t[1] = bb.y - (r[3] * bb.x + r[4] * bb.y + r[5] * bb.z);
+            t[2] = bb.z - (r[6] * bb.x + r[7] * bb.y + r[8] * bb.z);
+            const int4 fr = __ldg(L.frag + lane + 1);
+            parent = fr.z;
+            depth = fr.w;
+        }
+        for (int d = 1; d <= L.max_depth; ++d) {
+            __syncwarp();
+            if (lane < T && depth == d) {
+                for (int row = 0; row < 3; ++row) {
+                    const float4 p = M[3 * parent + row];
+                    M[3 * (lane + 1) + row] =
+                        make_float4(p.x * r[0] + p.y * r[3] + p.z * r[6], p.x * r[1] + p.y * r[4] + p.z * r[7],
+                                    p.x * r[2] + p.y * r[5] + p.z * r[8], p.x * t[0] + p.y * t[1] + p.z * t[2] + p.w);
+                }
+            }
+        }
+        __syncwarp();
+        for (int i = lane; i < L.n_atoms; i += 32) {
+            const float4 p = __ldg(L.ref + i);
+            const int f = __ldg(L.meta + i) >> 8;
+            const float4 m0 = M[3 * f], m1 = M[3 * f + 1], m2 = M[3 * f + 2];
+            float *o = xyz + ((size_t)b * L.n_atoms + __ldg(L.perm + i)) * 3;
+            o[0] = g[0] + fmaf(m0.x, p.x, fmaf(m0.y, p.y, fmaf(m0.z, p.z, m0.w)));
+            o[1] = g[1] + fmaf(m1.x, p.x, fmaf(m1.y, p.y, fmaf(m1.z, p.z, m1.w)));
+            o[2] = g[2] + fmaf(m2.x, p.x, fmaf(m2.y, p.y, fmaf(m2.z, p.z, m2.w)));
+        }
+        __syncwarp();
+    }
+}
+
+template <typename K>
+cudaError_t launch_warps(dock_ctx *ctx, K kernel, int B, int wpb, size_t smem, cudaStream_t s, const char *name,
+                         void **args) {
+    if (B <= 0) return cudaSuccess;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, wpb * 32, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const int need = (B + wpb - 1) / wpb;
+    const int cap = per_sm * ctx->num_sms;
+    const int blocks = need < cap ? need : cap;
+    TimedLaunch tl;
+    timing_begin(ctx, kernel_id(ctx, name), s, &tl);
+    e = cudaLaunchKernel((const void *)kernel, dim3(blocks), dim3(wpb * 32), args, smem, s);
+    timing_end(ctx, s, &tl);
+    ++ctx->launches;
+    return e;
+}
+
+// Warps per block: four when their scratch fits in shared memory, else fewer.
+int pick_warps(dock_ctx *ctx, const WarpLayout &W) {
+    for (int w = kScoreWarps; w > 1; w >>= 1)
+        if (evaluator_smem_ok(ctx, W, w)) return w;
+    return 1;
+}
+
+}  // namespace
+
+cudaError_t launch_score(dock_ctx *ctx, const LigandDev &L, const GridDev &G, const float *geno, int B, float *E,
+                         float *grad, cudaStream_t s) {
+    const bool g = grad != nullptr;
+    WarpLayout W = warp_layout(L.n_atoms, L.n_frag, L.n_pairs, g);
+    const int wpb = pick_warps(ctx, W);
+    const size_t smem = (size_t)W.total * sizeof(float) * wpb;
+    LigandDev l = L;
+    GridDev gg = G;
+    const float *gp = geno;
+    float *ep = E, *grp = grad;
+    void *args[] = {&l, &gg, &gp, &B, &ep, &grp, &W};
+    if (g) return launch_warps(ctx, score_kernel<true>, B, wpb, smem, s, "score_grad", args);
+    return launch_warps(ctx, score_kernel<false>, B, wpb, smem, s, "score", args);
+}
+
+cudaError_t launch_pose(dock_ctx *ctx, const LigandDev &L, const float *geno, int B, float *xyz, cudaStream_t s) {
+    WarpLayout W = warp_layout(L.n_atoms, L.n_frag, L.n_pairs, false);
+    const int wpb = pick_warps(ctx, W);
+    const size_t smem = (size_t)W.total * sizeof(float) * wpb;
+    LigandDev l = L;
+    const float *gp = geno;
+    float *xp = xyz;
+    void *args[] = {&l, &gp, &B, &xp, &W};
+    return launch_warps(ctx, pose_kernel, B, wpb, smem, s, "pose", args);
+}
+
+int evaluator_smem_ok(dock_ctx *ctx, const WarpLayout &w, int warps) {
+    return (size_t)w.total * sizeof(float) * warps <= ctx->smem_optin;
+}
+
+// ---------------------------------------------------------------------------
+// FP64 re-score of final poses: one thread per genotype, the energy written
+// out serially in double (same forms and constants as the FP32 evaluator).
+
+namespace {
+
+__device__ double interp64(const GridDev &G, int m, const double *u, double &pen) {
+    const int n[3] = {G.nx, G.ny, G.nz};
+    int i0[3];
+    double f[3];
+    for (int a = 0; a < 3; ++a) {
+        double v = u[a], d = 0.0;
+        if (v < 0.0) { d = v; v = 0.0; }
+        else if (v > n[a] - 1) { d = v - (n[a] - 1); v = n[a] - 1; }
+        int k = (int)floor(v);
+        if (k > n[a] - 2) k = n[a] - 2;
+        i0[a] = k;
+        f[a] = v - k;
+        const double dh = d * G.h64;
+        pen += 10.0 * dh * dh;
+    }
+    const int cell = (i0[2] * (G.ny - 1) + i0[1]) * (G.nx - 1) + i0[0];
+    const float4 a = G.cells[2 * ((size_t)cell * G.M + m)], b = G.cells[2 * ((size_t)cell * G.M + m) + 1];
+    const double v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+    double s = 0.0;
+    for (int c = 0; c < 8; ++c) {
+        const double wx = (c & 1) ? f[0] : 1.0 - f[0];
+        const double wy = (c & 2) ? f[1] : 1.0 - f[1];
+        const double wz = (c & 4) ? f[2] : 1.0 - f[2];
+        s += wx * wy * wz * v[c];
+    }
+    return s;
+}
+
+__global__ void rescore64_kernel(LigandDev L, GridDev G, const float *__restrict__ geno, int B, double *E) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    const float *g = geno + (size_t)b * L.n_genes;
+    double M[DOCK_MAX_TORSIONS + 1][12];
+    double qw = g[3], qx = g[4], qy = g[5], qz = g[6];
+    const double qn = sqrt(qw * qw + qx * qx + qy * qy + qz * qz);
+    if (qn >= 1e-12) { qw /= qn; qx /= qn; qy /= qn; qz /= qn; }
+    else { qw = 1; qx = qy = qz = 0; }
+    const double R0[12] = {1 - 2 * (qy * qy + qz * qz), 2 * (qx * qy - qw * qz), 2 * (qx * qz + qw * qy), 0,
+                           2 * (qx * qy + qw * qz), 1 - 2 * (qx * qx + qz * qz), 2 * (qy * qz - qw * qx), 0,
+                           2 * (qx * qz - qw * qy), 2 * (qy * qz + qw * qx), 1 - 2 * (qx * qx + qy * qy), 0};
+    for (int k = 0; k < 12; ++k) M[0][k] = R0[k];
+    // fragments are in depth-first preorder: a parent precedes its children
+    for (int f = 1; f < L.n_frag; ++f) {
+        const int k = f - 1;
+        const int2 ab = L.tors_ab[k];
+        const double *pa = L.ref64 + 3 * ab.x, *pb = L.ref64 + 3 * ab.y;
+        double u[3] = {pb[0] - pa[0], pb[1] - pa[1], pb[2] - pa[2]};
+        const double il = 1.0 / sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+        u[0] *= il; u[1] *= il; u[2] *= il;
+        double s, c;
+        sincos((double)g[L.tors_gene[k]], &s, &c);
+        const double oc = 1 - c;
+        const double r[9] = {c + oc * u[0] * u[0],        oc * u[0] * u[1] - s * u[2], oc * u[0] * u[2] + s * u[1],
+                             oc * u[1] * u[0] + s * u[2], c + oc * u[1] * u[1],        oc * u[1] * u[2] - s * u[0],
+                             oc * u[2] * u[0] - s * u[1], oc * u[2] * u[1] + s * u[0], c + oc * u[2] * u[2]};
+        const double t[3] = {pb[0] - (r[0] * pb[0] + r[1] * pb[1] + r[2] * pb[2]),
+                             pb[1] - (r[3] * pb[0] + r[4] * pb[1] + r[5] * pb[2]),
+                             pb[2] - (r[6] * pb[0] + r[7] * pb[1] + r[8] * pb[2])};
+        const double *P = M[L.frag[f].z];
+        for (int row = 0; row < 3; ++row) {
+            const double *pr = P + 4 * row;
+            M[f][4 * row + 0] = pr[0] * r[0] + pr[1] * r[3] + pr[2] * r[6];
+            M[f][4 * row + 1] = pr[0] * r[1] + pr[1] * r[4] + pr[2] * r[7];
+            M[f][4 * row + 2] = pr[0] * r[2] + pr[1] * r[5] + pr[2] * r[8];
+            M[f][4 * row + 3] = pr[0] * t[0] + pr[1] * t[1] + pr[2] * t[2] + pr[3];
+        }
+    }
+    double X[DOCK_MAX_ATOMS][3];
+    double e = 0.0;
+    for (int i = 0; i < L.n_atoms; ++i) {
+        const double *p = L.ref64 + 3 * i;
+        const int meta = L.meta[i];
+        const double *m = M[meta >> 8];
+        double u[3];
+        for (int a = 0; a < 3; ++a) {
+            X[i][a] = m[4 * a] * p[0] + m[4 * a + 1] * p[1] + m[4 * a + 2] * p[2] + m[4 * a + 3] + (double)g[a];
+        }
+        u[0] = (X[i][0] - G.ox64) / G.h64;
+        u[1] = (X[i][1] - G.oy64) / G.h64;
+        u[2] = (X[i][2] - G.oz64) / G.h64;
+        const double q = L.q64[i];
+        double pen = 0.0, dummy = 0.0;
+        e += interp64(G, G.map_of_type[meta & 255], u, pen) + q * interp64(G, G.emap, u, dummy) +
+             fabs(q) * interp64(G, G.dmap, u, dummy) + pen;
+    }
+    const double lb = 0.003627 * (78.4 + 8.5525);
+    for (int p = 0; p < L.n_pairs; ++p) {
+        const uint32_t ij = L.pair_ij[p];
+        const double *xi = X[ij & 0xffff], *xj = X[ij >> 16];
+        const double dx = xi[0] - xj[0], dy = xi[1] - xj[1], dz = xi[2] - xj[2];
+        double r = sqrt(dx * dx + dy * dy + dz * dz);
+        if (r >= 8.0) continue;
+        if (r < 0.5) r = 0.5;
+        const double *c = L.pair_c64 + 5 * p;
+        const double ri2 = 1.0 / (r * r), ri6 = ri2 * ri2 * ri2;
+        const double eps = -8.5525 + (78.4 + 8.5525) / (1.0 + 7.7839 * exp(-lb * r));
+        e += c[0] * ri6 * ri6 - c[1] * ri6 - c[2] * ri6 * ri2 * ri2 + c[3] / (eps * r) +
+             c[4] * exp(-r * r / (2.0 * 3.6 * 3.6));
+    }
+    E[b] = e;
+}
+
+}  // namespace
+
+cudaError_t launch_rescore64(dock_ctx *ctx, const LigandDev &L, const GridDev &G, const float *geno, int B, double *E,
+                             cudaStream_t s) {
+    if (B <= 0) return cudaSuccess;
+    TimedLaunch tl;
+    timing_begin(ctx, kernel_id(ctx, "rescore64"), s, &tl);
+    rescore64_kernel<<<(B + 63) / 64, 64, 0, s>>>(L, G, geno, B, E);
+    timing_end(ctx, s, &tl);
+    ++ctx->launches;
+    return cudaGetLastError();
+}

@@ -1,0 +1,647 @@
+// search.cu -- the Lamarckian genetic algorithm on the device (paper,
+// Section II-A): initial population, elitism + tournament selection +
+// two-point crossover + mutation, local-search sampling, ADADELTA local
+// search with Lamarckian write-back, per-run evaluation counting (the
+// per-run sum of Listing 1, folded into the kernels), and the driver that
+// runs generations until the budget is spent.
+//
+// Genetic operators act on FP32 genes with one IEEE round-to-nearest
+// operation per step (__fadd_rn & co., never contracted), so that given the
+// same energies and the same Philox stream they are reproducible exactly by
+// any IEEE single-precision implementation.
+#include <math.h>
+
+#include <algorithm>
+
+#include "eval.cuh"
+
+namespace {
+
+constexpr int kMaxLs = 256;
+constexpr float kPiF = 3.14159265358979323846f;
+constexpr float kTwoPiF = 6.28318530717958647692f;
+enum : uint32_t { kInit = 1, kSelect = 2, kCross = 3, kMutate = 4, kLsPick = 5 };
+
+struct GaConst {
+    int pop, nruns, nt;
+    float p_tour, p_cross, p_mut, trans_mut;
+    uint2 key;
+};
+
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32 -> 64-bit
+// products with a Weyl-sequence key schedule.
+__device__ __forceinline__ uint4 philox(uint4 c, uint2 k) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k.x += 0x9E3779B9u;
+            k.y += 0xBB67AE85u;
+        }
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+
+__device__ __forceinline__ uint4 draw4(uint2 key, uint32_t run, uint32_t gen, uint32_t entity, uint32_t purpose,
+                                       uint32_t draw) {
+    return philox(make_uint4((purpose << 16) | draw, entity, gen, run), key);
+}
+
+__device__ __forceinline__ uint32_t word(const uint4 &w, int i) {
+    return i == 0 ? w.x : i == 1 ? w.y : i == 2 ? w.z : w.w;
+}
+
+// top 24 bits * 2^-24: exact in FP32
+__device__ __forceinline__ float unif(uint32_t w) { return __fmul_rn((float)(w >> 8), 0x1p-24f); }
+__device__ __forceinline__ uint32_t uidx(uint32_t w, uint32_t n) {
+    return (uint32_t)(((unsigned long long)(w >> 8) * n) >> 24);
+}
+
+__device__ __forceinline__ float wrap_tau(float x) {
+    if (x >= kPiF) x = __fsub_rn(x, kTwoPiF);
+    else if (x < -kPiF) x = __fadd_rn(x, kTwoPiF);
+    return x;
+}
+
+__device__ __forceinline__ int block_of_gene(int j) { return j < 3 ? j : (j < 7 ? 3 : j - 3); }
+
+// Lexicographic (energy, index) minimum over the warp; every lane gets it.
+__device__ __forceinline__ void warp_argmin(float &e, int &i) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float e2 = __shfl_xor_sync(0xffffffffu, e, o);
+        const int i2 = __shfl_xor_sync(0xffffffffu, i, o);
+        if (e2 < e || (e2 == e && i2 < i)) {
+            e = e2;
+            i = i2;
+        }
+    }
+}
+
+__device__ int run_argmin(const float *E, int pop, int lane, float &best) {
+    float be = INFINITY;
+    int bi = 0x7fffffff;
+    for (int i = lane; i < pop; i += 32) {
+        const float e = E[i];
+        if (e < be || (e == be && i < bi)) {
+            be = e;
+            bi = i;
+        }
+    }
+    warp_argmin(be, bi);
+    best = be;
+    return bi;
+}
+
+// Generation-0 individual: translation uniform in the grid box, orientation
+// uniform on S^3 (Marsaglia 1972: two points in the unit disc), torsions
+// uniform in [-pi, pi).
+__device__ void init_individual(const GaConst &C, const GridDev &G, uint32_t run, uint32_t slot, float *gene) {
+    uint4 w = draw4(C.key, run, 0, slot, kInit, 0);
+    gene[0] = __fadd_rn(G.box_lo[0], __fmul_rn(unif(w.x), G.box_len[0]));
+    gene[1] = __fadd_rn(G.box_lo[1], __fmul_rn(unif(w.y), G.box_len[1]));
+    gene[2] = __fadd_rn(G.box_lo[2], __fmul_rn(unif(w.z), G.box_len[2]));
+    gene[3] = 1.f;
+    gene[4] = gene[5] = gene[6] = 0.f;
+    for (uint32_t att = 0; att < 32; ++att) {
+        w = draw4(C.key, run, 0, slot, kInit, 1 + att);
+        const float x1 = __fsub_rn(__fmul_rn(2.f, unif(w.x)), 1.f), x2 = __fsub_rn(__fmul_rn(2.f, unif(w.y)), 1.f);
+        const float x3 = __fsub_rn(__fmul_rn(2.f, unif(w.z)), 1.f), x4 = __fsub_rn(__fmul_rn(2.f, unif(w.w)), 1.f);
+        const float s1 = __fadd_rn(__fmul_rn(x1, x1), __fmul_rn(x2, x2));
+        const float s2 = __fadd_rn(__fmul_rn(x3, x3), __fmul_rn(x4, x4));
+        if (s1 < 1.f && s2 < 1.f && s2 > 0.f) {
+            const float f = __fsqrt_rn(__fdiv_rn(__fsub_rn(1.f, s1), s2));
+            gene[3] = x1;
+            gene[4] = x2;
+            gene[5] = __fmul_rn(x3, f);
+            gene[6] = __fmul_rn(x4, f);
+            break;
+        }
+    }
+    for (int k = 0; k < C.nt; ++k) {
+        if ((k & 3) == 0) w = draw4(C.key, run, 0, slot, kInit, 64 + (uint32_t)(k >> 2));
+        gene[7 + k] = __fsub_rn(__fmul_rn(unif(word(w, k & 3)), kTwoPiF), kPiF);
+    }
+}
+
+__device__ __forceinline__ int tournament(const float *E, int pop, float p_tour, uint4 w) {
+    const int i1 = (int)uidx(w.x, (uint32_t)pop), i2 = (int)uidx(w.y, (uint32_t)pop);
+    int better = i2, worse = i1;
+    if (E[i1] < E[i2] || (E[i1] == E[i2] && i1 <= i2)) {
+        better = i1;
+        worse = i2;
+    }
+    return unif(w.z) < p_tour ? better : worse;
+}
+
+template <bool EVAL>
+__global__ void __launch_bounds__(128)
+init_kernel(LigandDev L, GridDev G, GaConst C, float *pop_out, float *E_out, unsigned long long *evals, WarpLayout W) {
+    extern __shared__ float4 smem4[];
+    float *ws = reinterpret_cast<float *>(smem4) + (threadIdx.x >> 5) * W.total;
+    const int lane = threadIdx.x & 31;
+    const int item = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (item >= C.nruns * C.pop) return;
+    const int r = item / C.pop, s = item % C.pop, Gn = 7 + C.nt;
+    if (lane == 0) init_individual(C, G, (uint32_t)r, (uint32_t)s, ws + W.geno);
+    __syncwarp();
+    float *out = pop_out + (size_t)item * Gn;
+    for (int j = lane; j < Gn; j += 32) out[j] = ws[W.geno + j];
+    if (EVAL) {
+        const float e = dev::eval_warp<false>(L, G, ws, W, lane);
+        if (lane == 0) {
+            E_out[item] = e;
+            if (s == 0) atomicAdd(evals + r, (unsigned long long)C.pop);
+        }
+    }
+}
+
+// One warp builds one child (slot s of run r) and, with EVAL, scores it.
+template <bool EVAL>
+__global__ void __launch_bounds__(128)
+ga_kernel(LigandDev L, GridDev G, GaConst C, uint32_t gen, const float *__restrict__ pop_old,
+          const float *__restrict__ E_old, float *__restrict__ pop_new, float *__restrict__ E_new,
+          long long *info, unsigned long long *evals, WarpLayout W) {
+    extern __shared__ float4 smem4[];
+    float *ws = reinterpret_cast<float *>(smem4) + (threadIdx.x >> 5) * W.total;
+    const int lane = threadIdx.x & 31;
+    const int item = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (item >= C.nruns * C.pop) return;
+    const int r = item / C.pop, s = item % C.pop, Gn = 7 + C.nt, nblk = 4 + C.nt;
+    const float *old = pop_old + (size_t)r * C.pop * Gn;
+    const float *Eo = E_old + (size_t)r * C.pop;
+    float *child = pop_new + (size_t)item * Gn;
+    float *gs = ws + W.geno;
+    if (s == 0) {  // elitism: the best old individual, not re-evaluated
+        float be;
+        const int bi = run_argmin(Eo, C.pop, lane, be);
+        for (int j = lane; j < Gn; j += 32) child[j] = old[(size_t)bi * Gn + j];
+        if (lane == 0) {
+            if (E_new) E_new[item] = be;
+            if (evals) atomicAdd(evals + r, (unsigned long long)(C.pop - 1));
+            if (info) {
+                long long *o = info + (size_t)item * 5;
+                o[0] = bi; o[1] = bi; o[2] = 0; o[3] = 0; o[4] = 0;
+            }
+        }
+        return;
+    }
+    int p1 = 0, p2 = 0, lo = 0, hi = 0;
+    unsigned long long mask = 0;
+    if (lane == 0) {
+        p1 = tournament(Eo, C.pop, C.p_tour, draw4(C.key, r, gen, s, kSelect, 0));
+        p2 = tournament(Eo, C.pop, C.p_tour, draw4(C.key, r, gen, s, kSelect, 1));
+        const uint4 w = draw4(C.key, r, gen, s, kCross, 0);
+        if (unif(w.x) < C.p_cross) {
+            const int c1 = (int)uidx(w.y, (uint32_t)nblk), c2 = (int)uidx(w.z, (uint32_t)nblk);
+            lo = min(c1, c2);
+            hi = max(c1, c2);
+        }
+        uint4 m = make_uint4(0, 0, 0, 0);
+        for (int b = 0; b < nblk; ++b) {
+            if ((b & 3) == 0) m = draw4(C.key, r, gen, s, kMutate, (uint32_t)(b >> 2));
+            if (unif(word(m, b & 3)) < C.p_mut) mask |= 1ull << b;
+        }
+    }
+    p1 = __shfl_sync(0xffffffffu, p1, 0);
+    p2 = __shfl_sync(0xffffffffu, p2, 0);
+    lo = __shfl_sync(0xffffffffu, lo, 0);
+    hi = __shfl_sync(0xffffffffu, hi, 0);
+    mask = __shfl_sync(0xffffffffu, mask, 0);
+    for (int j = lane; j < Gn; j += 32) {
+        const int b = block_of_gene(j);
+        gs[j] = old[(size_t)((b >= lo && b < hi) ? p2 : p1) * Gn + j];
+    }
+    __syncwarp();
+    for (int b = lane; b < nblk; b += 32) {
+        if (!((mask >> b) & 1ull)) continue;
+        const uint4 v = draw4(C.key, r, gen, s, kMutate, 16 + (uint32_t)b);
+        if (b < 3) {
+            const float delta = __fsub_rn(__fmul_rn(unif(v.x), __fmul_rn(2.f, C.trans_mut)), C.trans_mut);
+            gs[b] = __fadd_rn(gs[b], delta);
+        } else if (b == 3) {
+            // q <- normalise((1, v) (x) q), v uniform in [-1, 1)^3
+            const float vx = __fsub_rn(__fmul_rn(2.f, unif(v.x)), 1.f);
+            const float vy = __fsub_rn(__fmul_rn(2.f, unif(v.y)), 1.f);
+            const float vz = __fsub_rn(__fmul_rn(2.f, unif(v.z)), 1.f);
+            const float qw = gs[3], qx = gs[4], qy = gs[5], qz = gs[6];
+            const float nw = __fsub_rn(__fsub_rn(__fsub_rn(qw, __fmul_rn(vx, qx)), __fmul_rn(vy, qy)), __fmul_rn(vz, qz));
+            const float nx = __fsub_rn(__fadd_rn(__fadd_rn(qx, __fmul_rn(vx, qw)), __fmul_rn(vy, qz)), __fmul_rn(vz, qy));
+            const float ny = __fadd_rn(__fadd_rn(__fsub_rn(qy, __fmul_rn(vx, qz)), __fmul_rn(vy, qw)), __fmul_rn(vz, qx));
+            const float nz = __fadd_rn(__fsub_rn(__fadd_rn(qz, __fmul_rn(vx, qy)), __fmul_rn(vy, qx)), __fmul_rn(vz, qw));
+            const float n = __fsqrt_rn(__fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(nw, nw), __fmul_rn(nx, nx)), __fmul_rn(ny, ny)),
+                                                 __fmul_rn(nz, nz)));
+            gs[3] = __fdiv_rn(nw, n);
+            gs[4] = __fdiv_rn(nx, n);
+            gs[5] = __fdiv_rn(ny, n);
+            gs[6] = __fdiv_rn(nz, n);
+        } else {
+            const float delta = __fsub_rn(__fmul_rn(unif(v.x), kTwoPiF), kPiF);
+            gs[b + 3] = wrap_tau(__fadd_rn(gs[b + 3], delta));
+        }
+    }
+    __syncwarp();
+    for (int j = lane; j < Gn; j += 32) child[j] = gs[j];
+    if (info && lane == 0) {
+        long long *o = info + (size_t)item * 5;
+        o[0] = p1; o[1] = p2; o[2] = lo; o[3] = hi; o[4] = (long long)mask;
+    }
+    if (EVAL) {
+        const float e = dev::eval_warp<false>(L, G, ws, W, lane);
+        if (lane == 0) E_new[item] = e;
+    }
+}
+
+// The local-search sample of a generation: the first n_ls entries of a
+// partial Fisher-Yates shuffle of 0..pop-1, kept as a list of displaced
+// positions instead of a pop-sized array.
+__global__ void picks_kernel(int pop, int n_ls, int nruns, uint2 key, uint32_t gen, int *picks) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nruns) return;
+    int pos[2 * kMaxLs], val[2 * kMaxLs], cnt = 0;
+    for (int k = 0; k < n_ls; ++k) {
+        const uint32_t w = draw4(key, r, gen, k, kLsPick, 0).x;
+        const int j = k + (int)uidx(w, (uint32_t)(pop - k));
+        int vk = k, vj = j, ik = -1, ij = -1;
+        for (int e = 0; e < cnt; ++e) {
+            if (pos[e] == k) { vk = val[e]; ik = e; }
+            if (pos[e] == j) { vj = val[e]; ij = e; }
+        }
+        if (ik < 0) { ik = cnt++; pos[ik] = k; }
+        val[ik] = vj;
+        if (j != k) {
+            if (ij < 0) { ij = cnt++; pos[ij] = j; }
+            val[ij] = vk;
+        }
+        picks[r * n_ls + k] = vj;
+    }
+}
+
+__device__ __forceinline__ void adadelta(float &x, float g, float &eg2, float &edx2, float rho, float eps) {
+    eg2 = fmaf(rho, eg2, (1.f - rho) * g * g);
+    const float dx = -sqrtf(edx2 + eps) * rsqrtf(eg2 + eps) * g;
+    edx2 = fmaf(rho, edx2, (1.f - rho) * dx * dx);
+    x += dx;
+}
+
+__device__ __forceinline__ float wrap_any(float x) {
+    return x - kTwoPiF * floorf((x + kPiF) * (1.f / kTwoPiF));
+}
+
+// ADADELTA local search, one warp per chain.  With picks (inside dock):
+// chain c is pick c % n_ls of run c / n_ls, updated in place in the
+// population; without: chain c starts at x_in[c] and writes x_out[c].
+__global__ void __launch_bounds__(128)
+ls_kernel(LigandDev L, GridDev G, float *x_in, float *E_pop, const int *__restrict__ picks, int pop, int n_ls,
+          int nchains, int iters, float rho, float eps, float *x_out, float *E_out, unsigned long long *evals,
+          WarpLayout W) {
+    extern __shared__ float4 smem4[];
+    float *ws = reinterpret_cast<float *>(smem4) + (threadIdx.x >> 5) * W.total;
+    const int lane = threadIdx.x & 31;
+    const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (c >= nchains) return;
+    const int Gn = L.n_genes;
+    float *xi, *xo, *eo;
+    int run = 0;
+    if (picks) {
+        run = c / n_ls;
+        const int ind = __ldg(picks + c);
+        xi = x_in + ((size_t)run * pop + ind) * Gn;
+        xo = xi;
+        eo = E_pop + (size_t)run * pop + ind;
+    } else {
+        xi = x_in + (size_t)c * Gn;
+        xo = x_out + (size_t)c * Gn;
+        eo = E_out + c;
+    }
+    const int j0 = lane, j1 = lane + 32;
+    float x0 = j0 < Gn ? xi[j0] : 0.f, x1 = j1 < Gn ? xi[j1] : 0.f;
+    float b0 = x0, b1 = x1, best = INFINITY;
+    float g2a = 0.f, g2b = 0.f, d2a = 0.f, d2b = 0.f;
+    for (int it = 0; it < iters; ++it) {
+        if (j0 < Gn) ws[W.geno + j0] = x0;
+        if (j1 < Gn) ws[W.geno + j1] = x1;
+        __syncwarp();
+        const float e = dev::eval_warp<true>(L, G, ws, W, lane);
+        if (e < best) {
+            best = e;
+            b0 = x0;
+            b1 = x1;
+        }
+        if (j0 < Gn) {
+            adadelta(x0, ws[W.grad + j0], g2a, d2a, rho, eps);
+            if (j0 >= 7) x0 = wrap_any(x0);
+        }
+        if (j1 < Gn) {
+            adadelta(x1, ws[W.grad + j1], g2b, d2b, rho, eps);
+            x1 = wrap_any(x1);
+        }
+        __syncwarp();
+    }
+    const float q3 = __shfl_sync(0xffffffffu, b0, 3), q4 = __shfl_sync(0xffffffffu, b0, 4);
+    const float q5 = __shfl_sync(0xffffffffu, b0, 5), q6 = __shfl_sync(0xffffffffu, b0, 6);
+    const float n = sqrtf(((q3 * q3 + q4 * q4) + q5 * q5) + q6 * q6);
+    if (lane >= 3 && lane < 7 && n > 0.f) b0 = b0 / n;
+    if (j0 < Gn) xo[j0] = b0;
+    if (j1 < Gn) xo[j1] = b1;
+    if (lane == 0) {
+        *eo = best;
+        if (evals) atomicAdd(evals + run, (unsigned long long)iters);
+    }
+}
+
+// Best individual of each run, quaternion normalised (FP32, fixed order).
+__global__ void final_kernel(const float *__restrict__ pop, const float *__restrict__ E, int popn, int nruns, int Gn,
+                             float *best_geno, float *best_E) {
+    const int lane = threadIdx.x & 31;
+    const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (r >= nruns) return;
+    float be;
+    const int bi = run_argmin(E + (size_t)r * popn, popn, lane, be);
+    const float *g = pop + ((size_t)r * popn + bi) * Gn;
+    const float w = g[3], x = g[4], y = g[5], z = g[6];
+    const float n = __fsqrt_rn(__fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(w, w), __fmul_rn(x, x)), __fmul_rn(y, y)),
+                                         __fmul_rn(z, z)));
+    for (int j = lane; j < Gn; j += 32) {
+        float v = g[j];
+        if (j >= 3 && j < 7 && n > 0.f) v = __fdiv_rn(v, n);
+        best_geno[(size_t)r * Gn + j] = v;
+    }
+    if (lane == 0 && best_E) best_E[r] = be;
+}
+
+__global__ void evals_out_kernel(const unsigned long long *ev, int n, int64_t *out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (int64_t)ev[i];
+}
+
+__global__ void philox_kernel(const uint32_t *ctr, int n, uint2 key, uint32_t *out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint4 c = make_uint4(ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3]);
+    const uint4 o = philox(c, key);
+    out[4 * i] = o.x;
+    out[4 * i + 1] = o.y;
+    out[4 * i + 2] = o.z;
+    out[4 * i + 3] = o.w;
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+
+GaConst ga_const(const dock_params &p, int nt, int nruns, uint64_t seed) {
+    GaConst C;
+    C.pop = p.pop_size;
+    C.nruns = nruns;
+    C.nt = nt;
+    C.p_tour = p.p_tour;
+    C.p_cross = p.p_cross;
+    C.p_mut = p.p_mut;
+    C.trans_mut = p.trans_mut;
+    C.key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+    return C;
+}
+
+template <typename K>
+cudaError_t launch_items(dock_ctx *ctx, K kernel, int items, int warps, size_t smem, cudaStream_t s,
+                         const char *name, void **args) {
+    if (items <= 0) return cudaSuccess;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    TimedLaunch tl;
+    timing_begin(ctx, kernel_id(ctx, name), s, &tl);
+    cudaError_t e = cudaLaunchKernel((const void *)kernel, dim3((items + warps - 1) / warps), dim3(warps * 32), args,
+                                     smem, s);
+    timing_end(ctx, s, &tl);
+    ++ctx->launches;
+    return e;
+}
+
+int resolve_params(dock_ctx *ctx, const dock_params *in, dock_params &p) {
+    if (in) p = *in;
+    else dock_default_params(&p);
+    if (p.ls_count < 0) p.ls_count = (6 * p.pop_size + 99) / 100;
+    if (p.pop_size < 2 || p.pop_size > (1 << 20) || p.nruns < 1 || p.max_evals < 0 || p.ls_count > p.pop_size ||
+        p.ls_count > kMaxLs || p.ls_iters < 0 || !(p.rho >= 0.f && p.rho < 1.f) || !(p.eps > 0.f))
+        return set_err(ctx, DOCK_ERR_INVALID, "invalid dock_params");
+    return DOCK_OK;
+}
+
+// LS chains per block: one warp per block while chains are few (spreads them
+// over all SMs), four once there are several per SM.
+int ls_warps(const dock_ctx *ctx, int chains) { return chains >= 8 * ctx->num_sms ? 4 : 1; }
+
+}  // namespace
+
+extern "C" {
+
+int dock_async(dock_ctx *ctx, const dock_grids *grids, const dock_ligand *lig, const dock_params *params,
+               uint64_t seed, float *best_geno, float *best_E32, double *best_E, int64_t *evals_used, void *stream) {
+    if (!ctx || !grids || !lig || !best_geno) return ctx ? set_err(ctx, DOCK_ERR_INVALID, "null argument") : DOCK_ERR_INVALID;
+    dock_params P;
+    int rc = resolve_params(ctx, params, P);
+    if (rc) return rc;
+    if ((rc = check_maps(ctx, grids, lig))) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    const LigandDev &L = lig->dev;
+    const GridDev &G = grids->dev;
+    const int Gn = L.n_genes, pop = P.pop_size, R = P.nruns, nls = P.ls_count;
+    const WarpLayout Wn = warp_layout(L.n_atoms, L.n_frag, L.n_pairs, false);
+    const WarpLayout Wg = warp_layout(L.n_atoms, L.n_frag, L.n_pairs, true);
+    if (!evaluator_smem_ok(ctx, Wg, 1)) return set_err(ctx, DOCK_ERR_SIZE, "ligand too large for shared memory");
+    const int gw = evaluator_smem_ok(ctx, Wn, 4) ? 4 : 1;
+    const size_t items = (size_t)R * pop;
+    float *popA = (float *)dev_alloc(ctx, items * Gn * 4, s), *popB = (float *)dev_alloc(ctx, items * Gn * 4, s);
+    float *EA = (float *)dev_alloc(ctx, items * 4, s), *EB = (float *)dev_alloc(ctx, items * 4, s);
+    int *picks = (int *)dev_alloc(ctx, (size_t)R * (nls > 0 ? nls : 1) * 4, s);
+    unsigned long long *ev = (unsigned long long *)dev_alloc(ctx, (size_t)R * 8, s);
+    float *bE32 = best_E32 ? best_E32 : (float *)dev_alloc(ctx, (size_t)R * 4, s);
+    cudaError_t e = cudaSuccess;
+    if (!popA || !popB || !EA || !EB || !picks || !ev || !bE32) {
+        rc = set_err(ctx, DOCK_ERR_OOM, "device allocation failed in dock");
+        goto done;
+    }
+    {
+        GaConst C = ga_const(P, L.n_tors, R, seed);
+        LigandDev l = L;
+        GridDev g = G;
+        WarpLayout wn = Wn, wg = Wg;
+        e = cudaMemsetAsync(ev, 0, (size_t)R * 8, s);
+        {
+            void *a[] = {&l, &g, &C, &popA, &EA, &ev, &wn};
+            if (!e) e = launch_items(ctx, init_kernel<true>, (int)items, gw, (size_t)Wn.total * 4 * gw, s, "dock_init", a);
+        }
+        const long long per_gen = (long long)(pop - 1) + (long long)nls * P.ls_iters;
+        long long ngen = 0;
+        if (P.max_evals > pop) ngen = (P.max_evals - pop + per_gen - 1) / per_gen;
+        const int chains = R * nls, lw = ls_warps(ctx, chains);
+        long long *no_info = nullptr;
+        float *no_out = nullptr;
+        for (long long gen = 1; gen <= ngen && !e; ++gen) {
+            uint32_t g32 = (uint32_t)gen;
+            void *a[] = {&l, &g, &C, &g32, &popA, &EA, &popB, &EB, &no_info, &ev, &wn};
+            e = launch_items(ctx, ga_kernel<true>, (int)items, gw, (size_t)Wn.total * 4 * gw, s, "dock_ga", a);
+            if (!e && chains > 0 && P.ls_iters > 0) {
+                TimedLaunch tl;
+                timing_begin(ctx, kernel_id(ctx, "dock_picks"), s, &tl);
+                picks_kernel<<<(R + 63) / 64, 64, 0, s>>>(pop, nls, R, C.key, g32, picks);
+                timing_end(ctx, s, &tl);
+                ++ctx->launches;
+                e = cudaGetLastError();
+                int iters = P.ls_iters;
+                float rho = P.rho, eps = P.eps;
+                int nl = nls, ch = chains, popn = pop;
+                void *c[] = {&l, &g, &popB, &EB, &picks, &popn, &nl, &ch, &iters, &rho, &eps, &no_out, &no_out, &ev, &wg};
+                if (!e) e = launch_items(ctx, ls_kernel, chains, lw, (size_t)Wg.total * 4 * lw, s, "dock_ls", c);
+            }
+            std::swap(popA, popB);
+            std::swap(EA, EB);
+        }
+        if (!e) {
+            TimedLaunch tl;
+            timing_begin(ctx, kernel_id(ctx, "dock_final"), s, &tl);
+            final_kernel<<<(R + 3) / 4, 128, 0, s>>>(popA, EA, pop, R, Gn, best_geno, bE32);
+            timing_end(ctx, s, &tl);
+            ++ctx->launches;
+            e = cudaGetLastError();
+        }
+        if (!e && best_E) e = launch_rescore64(ctx, L, G, best_geno, R, best_E, s);
+        if (!e && evals_used) {
+            evals_out_kernel<<<(R + 127) / 128, 128, 0, s>>>(ev, R, evals_used);
+            ++ctx->launches;
+            e = cudaGetLastError();
+        }
+        if (e) rc = cuda_err(ctx, e, "dock kernels");
+    }
+done:
+    dev_free(ctx, popA, s);
+    dev_free(ctx, popB, s);
+    dev_free(ctx, EA, s);
+    dev_free(ctx, EB, s);
+    dev_free(ctx, picks, s);
+    dev_free(ctx, ev, s);
+    if (!best_E32) dev_free(ctx, bE32, s);
+    return rc;
+}
+
+int dock(dock_ctx *ctx, const dock_grids *grids, const dock_ligand *lig, const dock_params *params, uint64_t seed,
+         float *best_geno, double *best_E, int64_t *evals_used) {
+    if (!ctx || !grids || !lig || !best_geno) return ctx ? set_err(ctx, DOCK_ERR_INVALID, "null argument") : DOCK_ERR_INVALID;
+    dock_params P;
+    int rc = resolve_params(ctx, params, P);
+    if (rc) return rc;
+    cudaStream_t s = nullptr;
+    const int R = P.nruns, Gn = lig->dev.n_genes;
+    float *g = (float *)dev_alloc(ctx, (size_t)R * Gn * 4, s);
+    double *E = (double *)dev_alloc(ctx, (size_t)R * 8, s);
+    int64_t *ev = (int64_t *)dev_alloc(ctx, (size_t)R * 8, s);
+    if (!g || !E || !ev) {
+        rc = set_err(ctx, DOCK_ERR_OOM, "device allocation failed in dock");
+    } else {
+        rc = dock_async(ctx, grids, lig, &P, seed, g, nullptr, E, ev, s);
+        cudaError_t e = cudaSuccess;
+        if (!rc) e = cudaMemcpyAsync(best_geno, g, (size_t)R * Gn * 4, cudaMemcpyDeviceToHost, s);
+        if (!rc && !e && best_E) e = cudaMemcpyAsync(best_E, E, (size_t)R * 8, cudaMemcpyDeviceToHost, s);
+        if (!rc && !e && evals_used) e = cudaMemcpyAsync(evals_used, ev, (size_t)R * 8, cudaMemcpyDeviceToHost, s);
+        if (!rc && !e) e = cudaStreamSynchronize(s);
+        if (!rc && e) rc = cuda_err(ctx, e, "dock copies");
+    }
+    dev_free(ctx, g, s);
+    dev_free(ctx, E, s);
+    dev_free(ctx, ev, s);
+    return rc;
+}
+
+int dock_init_population(dock_ctx *ctx, const dock_grids *grids, int n_torsions, int pop, int nruns, uint64_t seed,
+                         float *pop_out, void *stream) {
+    if (!ctx || !grids || !pop_out || n_torsions < 0 || n_torsions > DOCK_MAX_TORSIONS || pop < 1 || nruns < 1)
+        return ctx ? set_err(ctx, DOCK_ERR_INVALID, "invalid argument") : DOCK_ERR_INVALID;
+    dock_params P;
+    dock_default_params(&P);
+    P.pop_size = pop;
+    GaConst C = ga_const(P, n_torsions, nruns, seed);
+    LigandDev l{};
+    GridDev g = grids->dev;
+    WarpLayout w = warp_layout(1, 1, 0, false);
+    float *no_e = nullptr;
+    unsigned long long *no_ev = nullptr;
+    void *a[] = {&l, &g, &C, &pop_out, &no_e, &no_ev, &w};
+    cudaError_t e = launch_items(ctx, init_kernel<false>, pop * nruns, 4, (size_t)w.total * 16, (cudaStream_t)stream,
+                                 "init_population", a);
+    return e ? cuda_err(ctx, e, "init kernel") : DOCK_OK;
+}
+
+int dock_ga_children(dock_ctx *ctx, int n_torsions, int pop, int nruns, const float *pop_old, const float *E_old,
+                     uint64_t seed, uint32_t generation, const dock_params *params, float *pop_new, int64_t *info,
+                     void *stream) {
+    if (!ctx || !pop_old || !E_old || !pop_new || n_torsions < 0 || n_torsions > DOCK_MAX_TORSIONS || pop < 2 ||
+        nruns < 1)
+        return ctx ? set_err(ctx, DOCK_ERR_INVALID, "invalid argument") : DOCK_ERR_INVALID;
+    dock_params P;
+    if (params) P = *params;
+    else dock_default_params(&P);
+    P.pop_size = pop;
+    GaConst C = ga_const(P, n_torsions, nruns, seed);
+    LigandDev l{};
+    GridDev g{};
+    WarpLayout w = warp_layout(1, 1, 0, false);
+    float *no_e = nullptr;
+    unsigned long long *no_ev = nullptr;
+    long long *inf = (long long *)info;
+    void *a[] = {&l, &g, &C, &generation, &pop_old, &E_old, &pop_new, &no_e, &inf, &no_ev, &w};
+    cudaError_t e = launch_items(ctx, ga_kernel<false>, pop * nruns, 4, (size_t)w.total * 16, (cudaStream_t)stream,
+                                 "ga_children", a);
+    return e ? cuda_err(ctx, e, "ga kernel") : DOCK_OK;
+}
+
+int dock_ls_picks(dock_ctx *ctx, int pop, int n_ls, int nruns, uint64_t seed, uint32_t generation, int *picks,
+                  void *stream) {
+    if (!ctx || !picks || pop < 1 || n_ls < 0 || n_ls > pop || n_ls > kMaxLs || nruns < 1)
+        return ctx ? set_err(ctx, DOCK_ERR_INVALID, "invalid argument") : DOCK_ERR_INVALID;
+    if (n_ls == 0) return DOCK_OK;
+    const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+    picks_kernel<<<(nruns + 63) / 64, 64, 0, (cudaStream_t)stream>>>(pop, n_ls, nruns, key, generation, picks);
+    ++ctx->launches;
+    cudaError_t e = cudaGetLastError();
+    return e ? cuda_err(ctx, e, "picks kernel") : DOCK_OK;
+}
+
+int dock_local_search(dock_ctx *ctx, const dock_grids *grids, const dock_ligand *lig, const float *x0, int B,
+                      int iters, float rho, float eps, float *x_best, float *E_best, void *stream) {
+    if (!ctx || !grids || !lig || (B > 0 && (!x0 || !x_best || !E_best)) || B < 0 || iters < 1 ||
+        !(rho >= 0.f && rho < 1.f) || !(eps > 0.f))
+        return ctx ? set_err(ctx, DOCK_ERR_INVALID, "invalid argument") : DOCK_ERR_INVALID;
+    int rc = check_maps(ctx, grids, lig);
+    if (rc) return rc;
+    if (B == 0) return DOCK_OK;
+    const LigandDev &L = lig->dev;
+    WarpLayout W = warp_layout(L.n_atoms, L.n_frag, L.n_pairs, true);
+    if (!evaluator_smem_ok(ctx, W, 1)) return set_err(ctx, DOCK_ERR_SIZE, "ligand too large for shared memory");
+    const int lw = ls_warps(ctx, B) == 4 && evaluator_smem_ok(ctx, W, 4) ? 4 : 1;
+    LigandDev l = L;
+    GridDev g = grids->dev;
+    float *xin = const_cast<float *>(x0);
+    float *no_pop = nullptr;
+    const int *no_picks = nullptr;
+    unsigned long long *no_ev = nullptr;
+    int zero = 0, one = 1;
+    void *a[] = {&l, &g, &xin, &no_pop, &no_picks, &zero, &one, &B, &iters, &rho, &eps, &x_best, &E_best, &no_ev, &W};
+    cudaError_t e = launch_items(ctx, ls_kernel, B, lw, (size_t)W.total * 4 * lw, (cudaStream_t)stream, "local_search", a);
+    return e ? cuda_err(ctx, e, "local search kernel") : DOCK_OK;
+}
+
+int dock_philox(dock_ctx *ctx, const uint32_t *ctr, int n, uint32_t key_lo, uint32_t key_hi, uint32_t *out,
+                void *stream) {
+    if (!ctx || n < 0 || (n > 0 && (!ctr || !out))) return ctx ? set_err(ctx, DOCK_ERR_INVALID, "invalid argument") : DOCK_ERR_INVALID;
+    if (n == 0) return DOCK_OK;
+    philox_kernel<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(ctr, n, make_uint2(key_lo, key_hi), out);
+    ++ctx->launches;
+    cudaError_t e = cudaGetLastError();
+    return e ? cuda_err(ctx, e, "philox kernel") : DOCK_OK;
+}
+
+}  // extern "C"

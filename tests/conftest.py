@@ -34,3 +34,33 @@ def small_system(oracle_mod):
     maps = oracle_mod.build_maps(rec, box)
     grid = oracle_mod.OracleGrid(maps.astype(np.float32), box)
     return dict(lig=lig, rec=rec, box=box, maps=maps, grid=grid, olig=oracle_mod.OracleLigand(lig))
+
+
+@pytest.fixture(scope="session")
+def gpu():
+    """CUDA library context (fails loudly when CUDA or libdock is missing)."""
+    from paper_2203_02096_gb300 import capi
+    ctx = capi.Context(0)
+    yield ctx
+    ctx.close()
+
+
+@pytest.fixture(scope="session")
+def drug_system(oracle_mod):
+    """40-atom / 10-torsion ligand in 64^3 x 9 maps from a 3000-atom receptor
+    (the drug-size workload's inputs), maps built by the oracle."""
+    from paper_2203_02096_gb300 import synth
+    w = synth.drug_ligand_workload()
+    maps = oracle_mod.build_maps(w.receptor, w.box)
+    grid = oracle_mod.OracleGrid(maps.astype(np.float32), w.box)
+    return dict(w=w, lig=w.ligand, box=w.box, rec=w.receptor, maps=grid.maps, grid=grid,
+                olig=oracle_mod.OracleLigand(w.ligand))
+
+
+@pytest.fixture(scope="session")
+def diff_system(oracle_mod, drug_system):
+    """64-atom / 16-torsion ligand in the same 64^3 grid set (differentiation workload)."""
+    from paper_2203_02096_gb300 import synth
+    lig = synth.make_ligand(64, 16, seed=0)
+    return dict(lig=lig, box=drug_system["box"], maps=drug_system["maps"], grid=drug_system["grid"],
+                olig=oracle_mod.OracleLigand(lig))

@@ -1,0 +1,128 @@
+"""GPU parity of the search: Philox stream, genetic operators bit-exact given
+the same energies, local-search sampling, ADADELTA local search and whole
+dockings (best-energy distributions) against the FP64 oracle."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2203_02096_gb300 import capi, synth
+from tests.tolerances import energy_tol
+
+pytestmark = pytest.mark.gpu
+
+SEED = 0x1234_5678_9ABC
+
+
+def test_philox_bit_exact(gpu, oracle_mod):
+    rng = np.random.default_rng(0)
+    ctr = rng.integers(0, 2 ** 32, size=(20000, 4), dtype=np.uint64).astype(np.uint32)
+    ctr[:3] = [[0, 0, 0, 0], [0xFFFFFFFF] * 4, [0x243F6A88, 0x85A308D3, 0x13198A2E, 0x03707344]]
+    for key in [(0, 0), (0xFFFFFFFF, 0xFFFFFFFF), (0xA4093822, 0x299F31D0), (12345, 678)]:
+        out = capi.dock_philox(gpu, torch.from_numpy(ctr.view(np.int32)).cuda(), *key).cpu().numpy().view(np.uint32)
+        ref = np.stack([oracle_mod.philox(c, key) for c in ctr])
+        assert np.array_equal(out, ref)
+
+
+def _params(**kw):
+    return capi.default_params(**kw)
+
+
+def _oparams(oracle_mod, p):
+    return oracle_mod.make_params(pop_size=p.pop_size, nruns=p.nruns, max_evals=p.max_evals, ls_iters=p.ls_iters,
+                                  rho=p.rho, eps=p.eps, p_tour=p.p_tour, p_cross=p.p_cross, p_mut=p.p_mut,
+                                  trans_mut=p.trans_mut, ls_count=(6 * p.pop_size + 99) // 100 if p.ls_count < 0 else p.ls_count)
+
+
+def test_init_population_bit_exact(gpu, oracle_mod, small_system):
+    box = small_system["box"]
+    G = capi.grids_from_maps(gpu, small_system["maps"], box)
+    nt = small_system["olig"].n_torsions
+    popg = capi.dock_init_population(gpu, G, nt, 150, 4, SEED).cpu().numpy()
+    for r in range(4):
+        ref = oracle_mod.init_population(nt, small_system["grid"], SEED, r, 150)
+        assert np.array_equal(popg[r].view(np.uint32), ref.view(np.uint32))
+
+
+@pytest.mark.parametrize("p_mut", [0.02, 0.35])
+@pytest.mark.parametrize("nt", [4, 32])
+def test_ga_children_bit_exact(gpu, oracle_mod, small_system, p_mut, nt):
+    """Same FP32 energies in, bit-identical children and operator decisions out."""
+    grid = small_system["grid"]
+    R, pop = 5, 150
+    pop_old = np.stack([oracle_mod.init_population(nt, grid, 99, r, pop) for r in range(R)])
+    rng = np.random.default_rng(nt)
+    E = rng.standard_normal((R, pop)).astype(np.float32)
+    E[:, 10] = E.min(axis=1)       # ties for the best
+    E[:, 20:30] = E[:, 20:21]      # ties among ordinary individuals
+    P = _params(p_mut=p_mut)
+    OP = _oparams(oracle_mod, P)
+    for gen in (1, 17, 4000):
+        kids, info = capi.dock_ga_children(gpu, nt, torch.from_numpy(pop_old).cuda(), torch.from_numpy(E).cuda(),
+                                           SEED, gen, P)
+        kids, info = kids.cpu().numpy(), info.cpu().numpy()
+        for r in range(R):
+            ref, rinfo, elite = oracle_mod.ga_children(nt, pop_old[r], E[r].astype(np.float64), SEED, r, gen, OP)
+            assert np.array_equal(info[r], rinfo)
+            assert np.array_equal(kids[r].view(np.uint32), ref.view(np.uint32))
+
+
+def test_ls_picks_bit_exact(gpu, oracle_mod):
+    for pop, n_ls in [(150, 9), (50, 50), (1000, 60), (7, 1)]:
+        for gen in (1, 2, 999):
+            got = capi.dock_ls_picks(gpu, pop, n_ls, 6, SEED, gen).cpu().numpy()
+            for r in range(6):
+                assert np.array_equal(got[r], oracle_mod.ls_picks(pop, n_ls, SEED, r, gen))
+
+
+def test_local_search_against_oracle(gpu, oracle_mod, drug_system):
+    """ADADELTA from the same 64 starts: every GPU search improves on its start,
+    its reported energy is the oracle's energy of the pose it returns, and the
+    GPU and oracle searches end at matching energies (FP32 vs FP64 paths)."""
+    L = capi.ligand_from(gpu, drug_system["lig"])
+    G = capi.grids_from_maps(gpu, drug_system["maps"], drug_system["box"])
+    olig, ogrid = drug_system["olig"], drug_system["grid"]
+    x0 = oracle_mod.init_population(olig.n_torsions, ogrid, 5, 0, 64)
+    xb, Eb = capi.dock_local_search(gpu, G, L, torch.from_numpy(x0).cuda(), iters=100)
+    xb, Eb = xb.cpu().numpy(), Eb.cpu().numpy().astype(np.float64)
+    E0 = olig.score_batch(ogrid, x0, with_grad=False)
+    assert np.all(Eb <= E0 + energy_tol(E0))
+    Er = olig.score_batch(ogrid, xb, with_grad=False)
+    F = np.stack([olig.atom_forces(ogrid, x.astype(np.float64))[1] for x in xb])
+    assert np.all(np.abs(Er - Eb) <= energy_tol(Er, F))
+    assert np.allclose(np.linalg.norm(xb[:, 3:7], axis=1), 1.0, atol=1e-6)
+    Eo = np.array([oracle_mod.local_search(olig, ogrid, x, 100)[0] for x in x0])
+    close = np.abs(Eb - Eo) <= np.maximum(1e-3 * np.abs(Eo), 1e-2)
+    assert close.mean() >= 0.75, (close.mean(), np.median(Eb), np.median(Eo))
+    assert abs(np.median(Eb) - np.median(Eo)) < 0.5
+
+
+def _ks(a, b):
+    a, b = np.sort(a), np.sort(b)
+    xs = np.concatenate([a, b])
+    return np.max(np.abs(np.searchsorted(a, xs, side="right") / len(a) - np.searchsorted(b, xs, side="right") / len(b)))
+
+
+def test_dock_small_ligand_workload(gpu, oracle_mod):
+    """The small-ligand workload in full (16 atoms, 40^3 x 7 maps, 10 runs x
+    100k evaluations): exact evaluation accounting, FP64 re-score equal to the
+    oracle's energy of the returned pose, deterministic, and best-energy
+    distribution matching the oracle's docking of the same inputs."""
+    w = synth.small_ligand_workload()
+    maps = oracle_mod.build_maps(w.receptor, w.box).astype(np.float32)
+    ogrid = oracle_mod.OracleGrid(maps, w.box)
+    olig = oracle_mod.OracleLigand(w.ligand)
+    L = capi.ligand_from(gpu, w.ligand)
+    G = capi.grids_from_maps(gpu, maps, w.box)
+    P = _params(pop_size=w.pop_size, nruns=w.nruns, max_evals=w.max_evals, ls_iters=w.ls_iters)
+    bg, bE, ev = capi.dock(gpu, G, L, P, w.seed)
+    bg2, bE2, ev2 = capi.dock(gpu, G, L, P, w.seed)
+    assert np.array_equal(bg, bg2) and np.array_equal(bE, bE2) and np.array_equal(ev, ev2)
+    og, oE, oev = oracle_mod.dock(olig, ogrid, _oparams(oracle_mod, P), w.seed)
+    assert np.array_equal(ev, oev)
+    assert np.all(ev >= w.max_evals)
+    rescored = olig.score_batch(ogrid, bg, with_grad=False)
+    assert np.allclose(bE, rescored, rtol=1e-9, atol=1e-9)
+    assert np.allclose(np.linalg.norm(bg[:, 3:7], axis=1), 1.0, atol=1e-6)
+    # distributions of the best energies over runs
+    assert abs(np.median(bE) - np.median(oE)) < 0.5, (np.sort(bE), np.sort(oE))
+    assert _ks(bE, oE) <= 0.7
