@@ -1,0 +1,401 @@
+"""Benchmark: Lamarckian-GA docking of the drug-size workload on GB300.
+
+One step = one full docking (every step of the hot path: pose build, grid
+and pair energies, analytic gradient, ADADELTA and the genetic operators) of
+a 40-atom / 10-torsion ligand against 64^3 x 9 receptor maps built from a
+3000-atom receptor: 50 runs x 2.5M evaluations, population 150, ADADELTA
+300 iterations on 6% of each generation.  Inputs are seeded synthetic data
+shaped like the paper's workloads.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  With N > 1 (launched by torchrun) every rank
+docks its own replica (its own seed); there is no exchange step, so the only
+collectives are the timing barrier and the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "score+grad evals/s (docking, all evaluations counted)"
+UNIT = "evals/s"
+L2_FLUSH_BYTES = 256 << 20
+
+# ---------------------------------------------------------------------------
+# algorithmic work per evaluation (counts of the method's FP32 operations;
+# an FMA counts as 2).  See the design notes for the derivation.
+
+
+def flops_score_grad(n_atoms: int, n_tors: int, n_pairs: int, n_pairs_in: float) -> float:
+    """Per score+gradient evaluation: torsion rotations and forward kinematics
+    153 per torsion; per atom 165 (pose 24, three trilinear reads with
+    gradient 108, combine 18, force/torque sums 15); per pair inside the 8 A
+    cutoff 77 (distance 8, energy terms 28, dE/dr 23, force gather 18), per
+    pair beyond it 8 (distance only); root transform 37."""
+    return 37.0 + 153.0 * n_tors + 165.0 * n_atoms + 77.0 * n_pairs_in + 8.0 * (n_pairs - n_pairs_in)
+
+
+def grid_bytes_per_eval(n_atoms: int) -> int:
+    """Algorithmic L2->SM bytes: 3 maps x 8 corners x 4 B per atom."""
+    return 96 * n_atoms
+
+
+# ---------------------------------------------------------------------------
+# distributed helpers (host logic, tested with gloo on CPU)
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def replica_seed(base_seed: int, rank: int) -> int:
+    """Each rank docks an independent replica of the workload."""
+    return base_seed + 1_000_003 * rank
+
+
+def max_over_ranks(x: float, device=None) -> float:
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x: float, device=None) -> float:
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) >= 9 and f[1].replace(".", "").isdigit():
+                    rows.append(f)
+        finally:
+            os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = np.array([float(r[1]) for r in rows])
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(float(r[2]) for r in rows)),
+                "reasons": reasons, "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows)}
+
+
+# ---------------------------------------------------------------------------
+# the workload
+
+def workload():
+    from paper_2203_02096_gb300 import synth
+    return synth.drug_ligand_workload()
+
+
+def config_dict(w, l2_note: str):
+    return {"workload": "plain docking, drug-size ligand", "ligand_atoms": w.ligand.n_atoms,
+            "torsions": w.ligand.n_torsions, "grid": f"{w.box.dims[0]}^3 x {w.box.n_maps} maps FP32",
+            "receptor_atoms": len(w.receptor.types), "nruns": w.nruns, "max_evals_per_run": w.max_evals,
+            "pop_size": w.pop_size, "local_search": f"ADADELTA {w.ls_iters} iterations on {w.ls_rate_pct}%",
+            "l2": l2_note}
+
+
+_ORACLE_INPUTS = {}
+
+
+def cpu_sample(w, target_s: float, seed: int = 0):
+    """The FP64 oracle as it stands, on this host's cores: one docking run per
+    core with a budget sized to about target_s of CPU work.  Returns (evals/s,
+    cores, sample description, wall seconds).  The oracle builds its own maps
+    (untimed, once)."""
+    import oracle
+    cores = os.cpu_count() or 1
+    if w.name not in _ORACLE_INPUTS:
+        maps = oracle.build_maps(w.receptor, w.box, nthreads=cores).astype(np.float32)
+        _ORACLE_INPUTS[w.name] = (oracle.OracleGrid(maps, w.box), oracle.OracleLigand(w.ligand))
+    grid, lig = _ORACLE_INPUTS[w.name]
+    # calibration: score+grad throughput on all cores
+    from paper_2203_02096_gb300 import synth
+    g = synth.make_genotypes(4 * cores * 50, lig.n_torsions, w.box, seed=1)
+    t0 = time.perf_counter()
+    lig.score_batch(grid, g, with_grad=True, nthreads=cores)
+    rate = len(g) / (time.perf_counter() - t0)
+    per_gen = (w.pop_size - 1) + ((w.ls_rate_pct * w.pop_size + 99) // 100) * w.ls_iters
+    budget = max(w.pop_size + per_gen, int(rate * target_s / cores))
+    P = oracle.make_params(pop_size=w.pop_size, nruns=cores, max_evals=budget, ls_iters=w.ls_iters,
+                           ls_rate_pct=w.ls_rate_pct)
+    t0 = time.perf_counter()
+    _, _, evals = oracle.dock(lig, grid, P, seed, nthreads=cores)
+    dt = time.perf_counter() - t0
+    desc = (f"{cores} docking runs x {int(evals[0])} evaluations of the drug-size workload (50 runs x 2.5M "
+            f"in full), FP64 oracle, one run per thread")
+    return float(evals.sum() / dt), cores, desc, dt
+
+
+# ---------------------------------------------------------------------------
+
+def run_reference(args):
+    """The oracle arm: the FP64 CPU oracle timed on the host cores."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    w = workload()
+    per_step = max(3.0, min(10.0, 150.0 / max(1, args.steps + args.warmup)))
+    vals, cores, desc, total = [], 1, "", 0.0
+    for k in range(args.warmup + args.steps):
+        v, cores, desc, dt = cpu_sample(w, per_step if k >= args.warmup else 1.0, seed=k)
+        if k >= args.warmup:
+            vals.append(v)
+            total += dt
+    value = float(np.mean(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(w, "n/a (CPU)"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2203_02096_gb300 import capi
+
+    rank, world, local = dist_env()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    w = workload()
+    ctx = capi.Context(local)
+    # setup (untimed): receptor maps on the device, ligand resident
+    G = capi.grids_from_receptor(ctx, w.receptor, w.box)
+    L = capi.ligand_from(ctx, w.ligand)
+    P = capi.default_params(pop_size=w.pop_size, nruns=w.nruns, max_evals=w.max_evals, ls_iters=w.ls_iters,
+                            ls_threads=args.ls_threads)
+    seed = replica_seed(w.seed, rank)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    out = None
+    for k in range(args.warmup):
+        out = capi.dock_async(ctx, G, L, P, seed + k, out=out)
+    torch.cuda.synchronize(dev)
+
+    # ---- timed region: K full dockings, L2 flushed between them
+    ctx.reset_timing()
+    ctx.set_timing(True)
+    launches0 = ctx.launch_count()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize(dev)
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            starts[k].record(stream)
+            out = capi.dock_async(ctx, G, L, P, seed + 100 + k, out=out)
+            ends[k].record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+    ctx.set_timing(False)
+    launches = ctx.launch_count() - launches0
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    evals_per_step = int(out["evals"].sum().item())
+    my_s = sum(step_ms) / 1e3
+    t_max = max_over_ranks(my_s, dev)
+    total_evals = sum_over_ranks(float(evals_per_step * args.steps), dev)
+    value = total_evals / t_max
+    ligands_per_hour = 3600.0 * sum_over_ranks(float(args.steps), dev) / t_max
+    ls_ms, ls_n = ctx.kernel_time("dock_ls")
+    ga_ms, ga_n = ctx.kernel_time("dock_ga")
+    clocks = clk.summary()
+
+    # algorithmic work of the dominant kernel (the ADADELTA local search)
+    nls = (w.ls_rate_pct * w.pop_size + 99) // 100
+    evals_per_ls_launch = w.nruns * nls * w.ls_iters
+    xyz = capi.pose_batch(ctx, L, out["best_geno"]).cpu().numpy()
+    pij = pair_list(w.ligand)
+    d = np.linalg.norm(xyz[:, pij[:, 0]] - xyz[:, pij[:, 1]], axis=2)
+    p_in = float((d < 8.0).sum(axis=1).mean())
+    f_eval = flops_score_grad(w.ligand.n_atoms, w.ligand.n_torsions, len(pij), p_in)
+    ls_avg_s = ls_ms / max(ls_n, 1) / 1e3
+    achieved = f_eval * evals_per_ls_launch / ls_avg_s / 1e12
+    peak = peak_fp32_tflops()
+
+    # ---- end to end through the public API with host buffers
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize(dev)
+    barrier()
+    t0 = time.perf_counter()
+    h2d = d2h = 0
+    e2e_evals = 0
+    for k in range(e2e_steps):
+        Lk = capi.ligand_from(ctx, w.ligand)
+        bg, bE, ev = capi.dock(ctx, G, Lk, P, seed + 200 + k)
+        e2e_evals += int(ev.sum())
+        Lk.free()
+        h2d = w.ligand.nbytes()
+        d2h = bg.nbytes + bE.nbytes + ev.nbytes
+    torch.cuda.synchronize(dev)
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dev)
+    e2e_value = sum_over_ranks(float(e2e_evals), dev) / e2e_s
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        v, cores, desc, _ = cpu_sample(w, args.cpu_seconds)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": float(np.mean(step_ms)), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": dict(config_dict(w, "flushed between steps (256 MB write, outside the step events)"),
+                           ls_threads=args.ls_threads or "auto"),
+            "ligands_per_hour": ligands_per_hour,
+            "roofline": {"bound": "alu", "kernel": "dock_ls (ADADELTA local search)", "achieved": achieved,
+                         "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 FLOP x 2070 MHz (recipe unit counts, "
+                                        "max SM clock of measured)",
+                         "flops_per_eval": f_eval, "evals_per_launch": evals_per_ls_launch,
+                         "launch_ms": ls_avg_s * 1e3, "launches": ls_n,
+                         "l2_bytes_per_eval": grid_bytes_per_eval(w.ligand.n_atoms),
+                         "l2_achieved_gbs": grid_bytes_per_eval(w.ligand.n_atoms) * evals_per_ls_launch / ls_avg_s / 1e9},
+            "kernel_share": {"dock_ls": ls_ms / sum(step_ms), "dock_ga": ga_ms / sum(step_ms)},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": int(launches),
+            "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
+            "cpu_baseline": cpu,
+            "best_energy_median": float(np.median(out["best_E"].cpu().numpy())),
+        }
+        print(json.dumps(line), flush=True)
+    for h in (L, G):
+        h.free()
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def pair_list(lig):
+    """Pairs of the ligand's intramolecular list (different rigid fragments,
+    >= 4 bonds apart), from the bond graph -- used to count how many pairs of
+    the docked poses fall inside the cutoff."""
+    n = lig.n_atoms
+    adj = [[] for _ in range(n)]
+    for (a, b), r in zip(lig.bonds, lig.rotatable):
+        adj[a].append((b, r))
+        adj[b].append((a, r))
+    frag = -np.ones(n, int)
+    for s in range(n):
+        if frag[s] >= 0:
+            continue
+        stack = [s]
+        frag[s] = s
+        while stack:
+            a = stack.pop()
+            for b, r in adj[a]:
+                if not r and frag[b] < 0:
+                    frag[b] = s
+                    stack.append(b)
+    out = []
+    for s in range(n):
+        dist = -np.ones(n, int)
+        dist[s] = 0
+        q = [s]
+        for a in q:
+            for b, _ in adj[a]:
+                if dist[b] < 0:
+                    dist[b] = dist[a] + 1
+                    q.append(b)
+        out += [(s, t) for t in range(s + 1, n) if frag[s] != frag[t] and dist[t] >= 4]
+    return np.asarray(out, dtype=int).reshape(-1, 2)
+
+
+def peak_fp32_tflops() -> float:
+    mhz = 2070.0
+    try:
+        mp = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        mhz = float(mp.get("sm_max_mhz", mhz))
+    except (OSError, ValueError):
+        pass
+    return 152 * 128 * 2 * mhz * 1e6 / 1e12
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--ls-threads", type=int, default=0, help="threads per local-search chain (0 = auto)")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -81,6 +81,9 @@ typedef struct {
     float p_cross;     /* two-point crossover probability, 0.8                      */
     float p_mut;       /* per-gene-block mutation probability, 0.02                 */
     float trans_mut;   /* translation mutation half-width (A), 2.0                  */
+    int ls_threads;    /* threads evaluating one local-search chain: 32, 64, 128,
+                          256, or 0 = chosen from the chain count (the paper's
+                          threads-per-block knob, Section V-B); default 0       */
 } dock_params;
 
 /* Library version (major*10000 + minor*100 + patch). */
@@ -182,7 +185,8 @@ int dock_async(dock_ctx *ctx, const dock_grids *grids, const dock_ligand *lig, c
  * parent 1, parent 2, crossover cut lo, cut hi, mutated-block mask.
  * dock_ls_picks: picks [nruns][n_ls], the individuals given a local search.
  * dock_local_search: ADADELTA from B start points x0 [B][G], iters
- * iterations each; x_best [B][G] (unit quaternion) and E_best [B].
+ * iterations each, `threads` per chain as in dock_params.ls_threads;
+ * x_best [B][G] (unit quaternion) and E_best [B].
  * dock_philox: out[n][4] = Philox4x32-10(ctr[n][4], key = (key_lo, key_hi)). */
 int dock_init_population(dock_ctx *ctx, const dock_grids *grids, int n_torsions, int pop, int nruns,
                          uint64_t seed, float *pop_out, void *stream);
@@ -192,7 +196,7 @@ int dock_ga_children(dock_ctx *ctx, int n_torsions, int pop, int nruns, const fl
 int dock_ls_picks(dock_ctx *ctx, int pop, int n_ls, int nruns, uint64_t seed, uint32_t generation, int *picks,
                   void *stream);
 int dock_local_search(dock_ctx *ctx, const dock_grids *grids, const dock_ligand *lig, const float *x0, int B,
-                      int iters, float rho, float eps, float *x_best, float *E_best, void *stream);
+                      int iters, float rho, float eps, int threads, float *x_best, float *E_best, void *stream);
 int dock_philox(dock_ctx *ctx, const uint32_t *ctr, int n, uint32_t key_lo, uint32_t key_hi, uint32_t *out,
                 void *stream);
 

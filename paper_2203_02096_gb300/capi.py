@@ -33,7 +33,8 @@ _P = C.POINTER
 
 class DockParams(C.Structure):
     _fields_ = [("pop_size", _i), ("nruns", _i), ("max_evals", _i64), ("ls_count", _i), ("ls_iters", _i),
-                ("rho", _f), ("eps", _f), ("p_tour", _f), ("p_cross", _f), ("p_mut", _f), ("trans_mut", _f)]
+                ("rho", _f), ("eps", _f), ("p_tour", _f), ("p_cross", _f), ("p_mut", _f), ("trans_mut", _f),
+                ("ls_threads", _i)]
 
 
 ALLOC_FN = C.CFUNCTYPE(_vp, _sz, _vp, _vp)
@@ -65,7 +66,7 @@ SIGNATURES = {
     "dock_init_population": (_i, [_vp, _vp, _i, _i, _i, _u64, _vp, _vp]),
     "dock_ga_children": (_i, [_vp, _i, _i, _i, _vp, _vp, _u64, _u32, _P(DockParams), _vp, _vp, _vp]),
     "dock_ls_picks": (_i, [_vp, _i, _i, _i, _u64, _u32, _vp, _vp]),
-    "dock_local_search": (_i, [_vp, _vp, _vp, _vp, _i, _i, _f, _f, _vp, _vp, _vp]),
+    "dock_local_search": (_i, [_vp, _vp, _vp, _vp, _i, _i, _f, _f, _i, _vp, _vp, _vp]),
     "dock_philox": (_i, [_vp, _vp, _i, _u32, _u32, _vp, _vp]),
     "dock_set_timing": (_i, [_vp, _i]),
     "dock_kernel_time": (_i, [_vp, C.c_char_p, _P(_d), _P(_i64)]),
@@ -342,12 +343,12 @@ def dock_ls_picks(ctx, pop, n_ls, nruns, seed, generation, stream=None):
     return out[:, :n_ls]
 
 
-def dock_local_search(ctx, grids, lig, x0: torch.Tensor, iters: int, rho=0.8, eps=1e-2, stream=None):
+def dock_local_search(ctx, grids, lig, x0: torch.Tensor, iters: int, rho=0.8, eps=1e-2, threads=0, stream=None):
     B = x0.shape[0]
     xb = torch.empty_like(x0)
     Eb = torch.empty(B, dtype=torch.float32, device=x0.device)
     ctx.check(ctx.lib.dock_local_search(ctx.h, grids.h, lig.h, _ptr(x0), B, int(iters), float(rho), float(eps),
-                                        _ptr(xb), _ptr(Eb), _stream(stream)), "dock_local_search")
+                                        int(threads), _ptr(xb), _ptr(Eb), _stream(stream)), "dock_local_search")
     return xb, Eb
 
 

@@ -1,15 +1,21 @@
-// eval.cuh -- one warp evaluates the energy (and gradient) of one genotype.
+// eval.cuh -- a team of W warps evaluates the energy (and gradient) of one
+// genotype.
 //
 // Steps (paper, Section II-A / IV-B): genotype -> pose by rotations along
 // the torsion tree; particle-grid energy by trilinear reads of the receptor
 // maps; intramolecular pair energy (vdW / H-bond, screened Coulomb,
 // desolvation); then the analytic genotype gradient.
 //
-// GB300 layout: the warp keeps its pose, forces and per-pair force scalars
-// in shared memory; ligand constants come through L1 (read-only path);
-// each atom-map read is one 32-byte sector of the cell-major grid copy,
-// L2-resident.  Every reduction has a fixed order (lane-strided partial sums,
-// then an xor butterfly), so results are bit-reproducible run to run.
+// W = 1 (one warp per genotype) serves the throughput paths, where there are
+// many more genotypes than warps; W = 2..8 serves the local search when the
+// independent chains are too few to fill the GPU: the team splits atoms,
+// pairs and force gathers, like the paper's threads-per-block knob.
+//
+// GB300 layout: pose, forces and per-pair force scalars live in shared
+// memory; ligand constants come through L1 (read-only path); each atom-map
+// read is one 32-byte sector of the cell-major grid copy, L2-resident.
+// Every reduction has a fixed order (strided partial sums, xor butterflies,
+// then warps in index order), so results are bit-reproducible run to run.
 #pragma once
 
 #include "internal.h"
@@ -29,6 +35,21 @@ constexpr float kKout = 10.0f;
 
 template <typename T>
 __device__ __forceinline__ T ldg(const T *p) { return __ldg(p); }
+
+// W warps evaluating one genotype.  W = 1: a warp, possibly one of several
+// independent teams in a block; W > 1: the whole block is the team.
+template <int W>
+struct Team {
+    static constexpr int kSize = 32 * W;
+    int rank;  // 0 .. 32W-1
+    __device__ __forceinline__ explicit Team(int r) : rank(r) {}
+    __device__ __forceinline__ int lane() const { return rank & 31; }
+    __device__ __forceinline__ int warp() const { return rank >> 5; }
+    __device__ __forceinline__ void sync() const {
+        if (W == 1) __syncwarp();
+        else __syncthreads();
+    }
+};
 
 // Where an atom sits in the grid: cell index, in-cell fractions, clamping
 // and the out-of-box penalty (energy and its gradient in kcal/mol/A).
@@ -138,13 +159,44 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
-// Evaluates the genotype stored at ws[W.geno ...]; returns E on every lane.
-// With GRAD, dE/dgenotype is left at ws[W.grad ...].
-template <bool GRAD>
-__device__ float eval_warp(const LigandDev &L, const GridDev &G, float *ws, const WarpLayout &W, const int lane) {
-    const float *geno = ws + W.geno;
-    float4 *M = reinterpret_cast<float4 *>(ws + W.M);
-    float4 *X = reinterpret_cast<float4 *>(ws + W.x);
+// Sum over groups of k consecutive lanes (k a power of two <= 32).
+__device__ __forceinline__ float group_sum(float v, int k) {
+    for (int o = k >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Team-wide sum, same bits on every thread: warp butterflies, then the warps'
+// partials added in warp order.
+template <int W>
+__device__ __forceinline__ float team_sum(const Team<W> &tm, float v, float *red) {
+    v = warp_sum(v);
+    if (W == 1) return v;
+    if (tm.lane() == 0) red[tm.warp()] = v;
+    tm.sync();
+    float s = red[0];
+#pragma unroll
+    for (int w = 1; w < W; ++w) s += red[w];
+    tm.sync();
+    return s;
+}
+
+// Largest power of two k <= 32 with items * k <= team size (at least 1).
+__device__ __forceinline__ int lanes_per_item(int items, int team) {
+    int k = 1;
+    while (k < 32 && items * 2 * k <= team) k <<= 1;
+    return k;
+}
+
+// Evaluates the genotype stored at ws[L.geno ...]; returns E on every thread
+// of the team.  With GRAD, dE/dgenotype is left at ws[L.grad ...].
+template <int W, bool GRAD>
+__device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, const EvalLayout &Y, const Team<W> &tm) {
+    constexpr int S = Team<W>::kSize;
+    const int r = tm.rank;
+    const float *geno = ws + Y.geno;
+    float4 *M = reinterpret_cast<float4 *>(ws + Y.M);
+    float4 *X = reinterpret_cast<float4 *>(ws + Y.x);
+    float *red = ws + Y.red;
     const int T = L.n_tors, N = L.n_atoms, P = L.n_pairs;
 
     // Rigid-body part: positions are kept relative to the translation t.
@@ -158,36 +210,36 @@ __device__ float eval_warp(const LigandDev &L, const GridDev &G, float *ws, cons
     } else {
         qw = 1.f; qx = qy = qz = 0.f;
     }
-    if (lane == 0) {
+    if (r == 0) {
         M[0] = make_float4(1.f - 2.f * (qy * qy + qz * qz), 2.f * (qx * qy - qw * qz), 2.f * (qx * qz + qw * qy), 0.f);
         M[1] = make_float4(2.f * (qx * qy + qw * qz), 1.f - 2.f * (qx * qx + qz * qz), 2.f * (qy * qz - qw * qx), 0.f);
         M[2] = make_float4(2.f * (qx * qz - qw * qy), 2.f * (qy * qz + qw * qx), 1.f - 2.f * (qx * qx + qy * qy), 0.f);
     }
-    // Lane k holds the local transform of torsion k: rotation by tau_k about
-    // the reference bond axis through atom b (Rodrigues, right-hand rule).
+    // Thread k < T holds the local transform of torsion k: rotation by tau_k
+    // about the reference bond axis through atom b (Rodrigues, right-hand rule).
     float r00 = 0, r01 = 0, r02 = 0, r10 = 0, r11 = 0, r12 = 0, r20 = 0, r21 = 0, r22 = 0, t0 = 0, t1 = 0, t2 = 0;
     int depth = 0, parent = 0;
-    if (lane < T) {
+    if (r < T) {
         float s, c;
-        sincosf(geno[ldg(L.tors_gene + lane)], &s, &c);
-        const float4 u = ldg(L.tors_u + lane), b = ldg(L.tors_b + lane);
+        sincosf(geno[ldg(L.tors_gene + r)], &s, &c);
+        const float4 u = ldg(L.tors_u + r), b = ldg(L.tors_b + r);
         const float oc = 1.f - c;
-        r00 = fmaf(oc * u.x, u.x, c);       r01 = fmaf(oc * u.x, u.y, -s * u.z); r02 = fmaf(oc * u.x, u.z, s * u.y);
-        r10 = fmaf(oc * u.y, u.x, s * u.z); r11 = fmaf(oc * u.y, u.y, c);       r12 = fmaf(oc * u.y, u.z, -s * u.x);
+        r00 = fmaf(oc * u.x, u.x, c);        r01 = fmaf(oc * u.x, u.y, -s * u.z); r02 = fmaf(oc * u.x, u.z, s * u.y);
+        r10 = fmaf(oc * u.y, u.x, s * u.z);  r11 = fmaf(oc * u.y, u.y, c);       r12 = fmaf(oc * u.y, u.z, -s * u.x);
         r20 = fmaf(oc * u.z, u.x, -s * u.y); r21 = fmaf(oc * u.z, u.y, s * u.x); r22 = fmaf(oc * u.z, u.z, c);
         t0 = b.x - (r00 * b.x + r01 * b.y + r02 * b.z);
         t1 = b.y - (r10 * b.x + r11 * b.y + r12 * b.z);
         t2 = b.z - (r20 * b.x + r21 * b.y + r22 * b.z);
-        const int4 fr = ldg(L.frag + lane + 1);
+        const int4 fr = ldg(L.frag + r + 1);
         parent = fr.z;
         depth = fr.w;
     }
     // Forward kinematics, one tree level at a time: M_child = M_parent o L_k.
     for (int d = 1; d <= L.max_depth; ++d) {
-        __syncwarp();
-        if (lane < T && depth == d) {
+        tm.sync();
+        if (r < T && depth == d) {
             const float4 p0 = M[3 * parent], p1 = M[3 * parent + 1], p2 = M[3 * parent + 2];
-            float4 *o = M + 3 * (lane + 1);
+            float4 *o = M + 3 * (r + 1);
             o[0] = make_float4(p0.x * r00 + p0.y * r10 + p0.z * r20, p0.x * r01 + p0.y * r11 + p0.z * r21,
                                p0.x * r02 + p0.y * r12 + p0.z * r22, p0.x * t0 + p0.y * t1 + p0.z * t2 + p0.w);
             o[1] = make_float4(p1.x * r00 + p1.y * r10 + p1.z * r20, p1.x * r01 + p1.y * r11 + p1.z * r21,
@@ -196,13 +248,13 @@ __device__ float eval_warp(const LigandDev &L, const GridDev &G, float *ws, cons
                                p2.x * r02 + p2.y * r12 + p2.z * r22, p2.x * t0 + p2.y * t1 + p2.z * t2 + p2.w);
         }
     }
-    __syncwarp();
+    tm.sync();
 
     // Atoms: position, then the particle-grid term.
     const float tux = (tx - G.ox) * G.inv_h, tuy = (ty - G.oy) * G.inv_h, tuz = (tz - G.oz) * G.inv_h;
-    float4 *Fv = reinterpret_cast<float4 *>(ws + W.f);
+    float4 *Fv = reinterpret_cast<float4 *>(ws + Y.f);
     float e = 0.f;
-    for (int i = lane; i < N; i += DOCK_WARP) {
+    for (int i = r; i < N; i += S) {
         const float4 p = ldg(L.ref + i);
         const int meta = ldg(L.meta + i);
         const int f = meta >> 8;
@@ -216,95 +268,109 @@ __device__ float eval_warp(const LigandDev &L, const GridDev &G, float *ws, cons
                                     fmaf(dy, G.inv_h, tuy), fmaf(dz, G.inv_h, tuz), g);
         if (GRAD) Fv[i] = make_float4(g.x, g.y, g.z, 0.f);
     }
-    __syncwarp();
+    tm.sync();
 
-    // Intramolecular pairs, lane-strided; s_p = (dE/dr)/r kept per pair.
-    float *S = ws + W.s;
-    for (int p = lane; p < P; p += DOCK_WARP) {
+    // Intramolecular pairs, strided over the team; s_p = (dE/dr)/r kept per pair.
+    float *Sp = ws + Y.s;
+    for (int p = r; p < P; p += S) {
         const uint32_t ij = ldg(L.pair_ij + p);
         const float4 xi = X[ij & 0xffffu], xj = X[ij >> 16];
         const float ddx = xi.x - xj.x, ddy = xi.y - xj.y, ddz = xi.z - xj.z;
         const float r2 = fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz));
         float s = 0.f;
         if (r2 < kCut2) e += pair_energy<GRAD>(r2, ldg(L.pair_c + p), ldg(L.pair_ds + p), s);
-        if (GRAD) S[p] = s;
+        if (GRAD) Sp[p] = s;
     }
-    e = warp_sum(e);
-    if (!GRAD) return e;
-    __syncwarp();
+    if (!GRAD) return team_sum(tm, e, red);
+    tm.sync();
 
-    // Forces: dE/dx_i += s_p (x_i - x_partner) over the atom's pairs, in CSR order.
-    for (int i = lane; i < N; i += DOCK_WARP) {
-        const float4 xi = X[i];
-        float4 fi = Fv[i];
-        const int e0 = ldg(L.adj_off + i), e1 = ldg(L.adj_off + i + 1);
-        for (int k = e0; k < e1; ++k) {
-            const uint32_t a = ldg(L.adj + k);
-            const float s = S[a & 0xffffu];
-            const float4 xo = X[a >> 16];
-            fi.x = fmaf(s, xi.x - xo.x, fi.x);
-            fi.y = fmaf(s, xi.y - xo.y, fi.y);
-            fi.z = fmaf(s, xi.z - xo.z, fi.z);
+    // Forces: dE/dx_i += s_p (x_i - x_partner) over the atom's pairs, each
+    // atom's CSR list split over k lanes, summed by a butterfly.  Per atom also
+    // (x_i - t) x f_i for the torque and torsion sums.
+    float4 *Tq = reinterpret_cast<float4 *>(ws + Y.tq);
+    {
+        const int k = lanes_per_item(N, S), per = S / k, sub = r & (k - 1);
+        for (int base = 0; base < N; base += per) {
+            const int i = base + r / k;
+            const bool act = i < N;
+            float fx = 0.f, fy = 0.f, fz = 0.f;
+            float4 xi = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (act) {
+                xi = X[i];
+                const int e1 = ldg(L.adj_off + i + 1);
+                for (int q = ldg(L.adj_off + i) + sub; q < e1; q += k) {
+                    const uint32_t a = ldg(L.adj + q);
+                    const float s = Sp[a & 0xffffu];
+                    const float4 xo = X[a >> 16];
+                    fx = fmaf(s, xi.x - xo.x, fx);
+                    fy = fmaf(s, xi.y - xo.y, fy);
+                    fz = fmaf(s, xi.z - xo.z, fz);
+                }
+            }
+            fx = group_sum(fx, k);
+            fy = group_sum(fy, k);
+            fz = group_sum(fz, k);
+            if (act && sub == 0) {
+                const float4 g = Fv[i];
+                fx += g.x; fy += g.y; fz += g.z;
+                Fv[i] = make_float4(fx, fy, fz, 0.f);
+                Tq[i] = make_float4(xi.y * fz - xi.z * fy, xi.z * fx - xi.x * fz, xi.x * fy - xi.y * fx, 0.f);
+            }
         }
-        Fv[i] = fi;
     }
-    __syncwarp();
+    tm.sync();
 
-    // Per-fragment sums of f_i and (x_i - t) x f_i.
-    float4 *FS = reinterpret_cast<float4 *>(ws + W.fs);
-    for (int f = lane; f < L.n_frag; f += DOCK_WARP) {
-        const int4 fr = ldg(L.frag + f);
-        float fx = 0, fy = 0, fz = 0, gx = 0, gy = 0, gz = 0;
-        for (int i = fr.x; i < fr.y; ++i) {
-            const float4 xi = X[i], fi = Fv[i];
-            fx += fi.x; fy += fi.y; fz += fi.z;
-            gx += xi.y * fi.z - xi.z * fi.y;
-            gy += xi.z * fi.x - xi.x * fi.z;
-            gz += xi.x * fi.y - xi.y * fi.x;
+    // Gradient: range k < T is the contiguous atom range torsion k moves,
+    // range T is the whole ligand (translation and rotation).  Each range is
+    // summed by m lanes and a butterfly.
+    float *grad = ws + Y.grad;
+    {
+        const int R = T + 1, m = lanes_per_item(R, S), per = S / m, sub = r & (m - 1);
+        for (int base = 0; base < R; base += per) {
+            const int k = base + r / m;
+            const bool act = k < R;
+            int lo = 0, hi = 0;
+            if (act) {
+                if (k < T) {
+                    const int2 rg = ldg(L.tors_range + k);
+                    lo = rg.x;
+                    hi = rg.y;
+                } else {
+                    hi = N;
+                }
+            }
+            float a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0, a5 = 0;
+            for (int i = lo + sub; i < hi; i += m) {
+                const float4 f = Fv[i], t = Tq[i];
+                a0 += f.x; a1 += f.y; a2 += f.z;
+                a3 += t.x; a4 += t.y; a5 += t.z;
+            }
+            a0 = group_sum(a0, m); a1 = group_sum(a1, m); a2 = group_sum(a2, m);
+            a3 = group_sum(a3, m); a4 = group_sum(a4, m); a5 = group_sum(a5, m);
+            if (act && sub == 0) {
+                if (k < T) {  // u_k . sum over the moved atoms of (x_i - x_b) x f_i
+                    const int2 ab = ldg(L.tors_ab + k);
+                    const float4 xa = X[ab.x], xb = X[ab.y];
+                    float ux = xb.x - xa.x, uy = xb.y - xa.y, uz = xb.z - xa.z;
+                    const float il = rsqrtf(fmaf(ux, ux, fmaf(uy, uy, uz * uz)));
+                    ux *= il; uy *= il; uz *= il;
+                    const float cx = a3 - (xb.y * a2 - xb.z * a1);
+                    const float cy = a4 - (xb.z * a0 - xb.x * a2);
+                    const float cz = a5 - (xb.x * a1 - xb.y * a0);
+                    grad[ldg(L.tors_gene + k)] = fmaf(ux, cx, fmaf(uy, cy, uz * cz));
+                } else {  // dE/dt = sum f; dE/dq = 2 ((0, G) (x) qhat) / |q|, G = torque about t
+                    grad[0] = a0; grad[1] = a1; grad[2] = a2;
+                    const float k2 = 2.f * qinv;
+                    grad[3] = k2 * (-a3 * qx - a4 * qy - a5 * qz);
+                    grad[4] = k2 * (a3 * qw + a4 * qz - a5 * qy);
+                    grad[5] = k2 * (-a3 * qz + a4 * qw + a5 * qx);
+                    grad[6] = k2 * (a3 * qy - a4 * qx + a5 * qw);
+                }
+            }
         }
-        FS[2 * f] = make_float4(fx, fy, fz, 0.f);
-        FS[2 * f + 1] = make_float4(gx, gy, gz, 0.f);
     }
-    __syncwarp();
-
-    float *grad = ws + W.grad;
-    // Torsion k: u_k . sum over its subtree of (x_i - x_b) x f_i.
-    if (lane < T) {
-        const int f0 = lane + 1, f1 = ldg(L.sub_end + f0);
-        float fx = 0, fy = 0, fz = 0, gx = 0, gy = 0, gz = 0;
-        for (int f = f0; f < f1; ++f) {
-            const float4 a = FS[2 * f], b = FS[2 * f + 1];
-            fx += a.x; fy += a.y; fz += a.z;
-            gx += b.x; gy += b.y; gz += b.z;
-        }
-        const int2 ab = ldg(L.tors_ab + lane);
-        const float4 xa = X[ab.x], xb = X[ab.y];
-        float ux = xb.x - xa.x, uy = xb.y - xa.y, uz = xb.z - xa.z;
-        const float il = rsqrtf(fmaf(ux, ux, fmaf(uy, uy, uz * uz)));
-        ux *= il; uy *= il; uz *= il;
-        const float cx = gx - (xb.y * fz - xb.z * fy);
-        const float cy = gy - (xb.z * fx - xb.x * fz);
-        const float cz = gz - (xb.x * fy - xb.y * fx);
-        grad[ldg(L.tors_gene + lane)] = fmaf(ux, cx, fmaf(uy, cy, uz * cz));
-    }
-    // Whole-ligand force and torque about t, fixed-order butterfly.
-    float a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0, a5 = 0;
-    for (int f = lane; f < L.n_frag; f += DOCK_WARP) {
-        const float4 a = FS[2 * f], b = FS[2 * f + 1];
-        a0 += a.x; a1 += a.y; a2 += a.z; a3 += b.x; a4 += b.y; a5 += b.z;
-    }
-    a0 = warp_sum(a0); a1 = warp_sum(a1); a2 = warp_sum(a2);
-    a3 = warp_sum(a3); a4 = warp_sum(a4); a5 = warp_sum(a5);
-    if (lane == 0) {
-        grad[0] = a0; grad[1] = a1; grad[2] = a2;
-        // dE/dq = 2 ((0, G) (x) qhat) / |q|
-        const float k2 = 2.f * qinv;
-        grad[3] = k2 * (-a3 * qx - a4 * qy - a5 * qz);
-        grad[4] = k2 * (a3 * qw + a4 * qz - a5 * qy);
-        grad[5] = k2 * (-a3 * qz + a4 * qw + a5 * qx);
-        grad[6] = k2 * (a3 * qy - a4 * qx + a5 * qw);
-    }
-    __syncwarp();
+    e = team_sum(tm, e, red);  // its barriers also publish grad[] (W > 1)
+    tm.sync();
     return e;
 }
 

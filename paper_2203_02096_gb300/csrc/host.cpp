@@ -113,6 +113,7 @@ void dock_default_params(dock_params *p) {
     p->p_cross = 0.8f;
     p->p_mut = 0.02f;
     p->trans_mut = 2.0f;
+    p->ls_threads = 0;
 }
 
 int dock_create(dock_ctx **out, int device, const dock_allocator *alloc) {
@@ -560,6 +561,9 @@ extern "C" int load_ligand(dock_ctx *ctx, int n, const double *xyz, const int *t
     const size_t o_tb = B.add(tb.data(), T * sizeof(float4));
     const size_t o_tab = B.add(tab.data(), T * sizeof(int2));
     const size_t o_tg = B.add(tgene.data(), T * sizeof(int));
+    std::vector<int2> trange(std::max(T, 1));
+    for (int k = 0; k < T; ++k) trange[k] = make_int2(frag[k + 1].x, frag[sub_end[k + 1] - 1].y);
+    const size_t o_trg = B.add(trange.data(), T * sizeof(int2));
     const size_t o_pij = B.add(pij.data(), P * sizeof(uint32_t));
     const size_t o_pc = B.add(pc.data(), P * sizeof(float4));
     const size_t o_pds = B.add(pds.data(), P * sizeof(float));
@@ -600,6 +604,7 @@ extern "C" int load_ligand(dock_ctx *ctx, int n, const double *xyz, const int *t
     d.tors_b = (const float4 *)(base + o_tb);
     d.tors_ab = (const int2 *)(base + o_tab);
     d.tors_gene = (const int *)(base + o_tg);
+    d.tors_range = (const int2 *)(base + o_trg);
     d.pair_ij = (const uint32_t *)(base + o_pij);
     d.pair_c = (const float4 *)(base + o_pc);
     d.pair_ds = (const float *)(base + o_pds);
@@ -643,7 +648,7 @@ static int score_common(dock_ctx *ctx, const dock_grids *g, const dock_ligand *l
     int rc = check_maps(ctx, g, l);
     if (rc) return rc;
     if (B == 0) return DOCK_OK;
-    const WarpLayout W = warp_layout(l->dev.n_atoms, l->dev.n_frag, l->dev.n_pairs, grad != nullptr);
+    const EvalLayout W = eval_layout(l->dev.n_atoms, l->dev.n_frag, l->dev.n_pairs, grad != nullptr);
     if (!evaluator_smem_ok(ctx, W, 1)) return set_err(ctx, DOCK_ERR_SIZE, "ligand too large for shared memory");
     cudaError_t e = launch_score(ctx, l->dev, g->dev, geno, B, E, grad, (cudaStream_t)stream);
     return e ? cuda_err(ctx, e, "score kernel") : DOCK_OK;
@@ -664,7 +669,7 @@ int pose_batch(dock_ctx *ctx, const dock_ligand *l, const float *geno, int B, fl
     if (!ctx) return DOCK_ERR_INVALID;
     if (!l || B < 0 || (B > 0 && (!geno || !xyz))) return set_err(ctx, DOCK_ERR_INVALID, "invalid argument");
     if (B == 0) return DOCK_OK;
-    const WarpLayout W = warp_layout(l->dev.n_atoms, l->dev.n_frag, l->dev.n_pairs, false);
+    const EvalLayout W = eval_layout(l->dev.n_atoms, l->dev.n_frag, l->dev.n_pairs, false);
     if (!evaluator_smem_ok(ctx, W, 1)) return set_err(ctx, DOCK_ERR_SIZE, "ligand too large for shared memory");
     cudaError_t e = launch_pose(ctx, l->dev, geno, B, xyz, (cudaStream_t)stream);
     return e ? cuda_err(ctx, e, "pose kernel") : DOCK_OK;

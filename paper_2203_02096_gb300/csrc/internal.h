@@ -23,6 +23,7 @@ struct LigandDev {
     const int *perm;          // [n] internal atom -> input atom
     const int4 *frag;         // [F] (atom begin, atom end, parent, depth)
     const int *sub_end;       // [F] end of the fragment's subtree (fragment numbering)
+    const int2 *tors_range;   // [T] contiguous atom range [x, y) that torsion k moves
     const float4 *tors_u;     // [T] unit bond axis a->b in the reference frame
     const float4 *tors_b;     // [T] reference position of axis atom b
     const int2 *tors_ab;      // [T] internal atom indices (a, b)
@@ -52,23 +53,24 @@ struct GridDev {
     double ox64, oy64, oz64, h64;
 };
 
-// Per-warp shared-memory scratch of the evaluator, offsets in floats (each a
+// Shared-memory scratch of one evaluating team, offsets in floats (each a
 // multiple of 4 so float4 views are aligned).
-struct WarpLayout {
-    int geno, grad, M, fs, x, f, s, total;
+struct EvalLayout {
+    int geno, grad, red, M, x, f, tq, s, total;
 };
 
 __host__ __device__ inline int round4(int v) { return (v + 3) & ~3; }
 
-__host__ __device__ inline WarpLayout warp_layout(int n_atoms, int n_frag, int n_pairs, bool grad) {
-    WarpLayout w;
+__host__ __device__ inline EvalLayout eval_layout(int n_atoms, int n_frag, int n_pairs, bool grad) {
+    EvalLayout w;
     int o = 0;
     w.geno = o; o += 48;
     w.grad = o; o += 48;
+    w.red = o; o += 32;
     w.M = o; o += 12 * n_frag;
-    w.fs = o; o += grad ? 8 * n_frag : 0;
     w.x = o; o += 4 * n_atoms;
     w.f = o; o += grad ? 4 * n_atoms : 0;
+    w.tq = o; o += grad ? 4 * n_atoms : 0;
     w.s = o; o += grad ? round4(n_pairs) : 0;
     w.total = round4(o);
     return w;
@@ -123,7 +125,7 @@ int kernel_id(dock_ctx *ctx, const char *name);
 void timing_begin(dock_ctx *ctx, int kid, cudaStream_t s, TimedLaunch *tl);
 void timing_end(dock_ctx *ctx, cudaStream_t s, TimedLaunch *tl);
 int check_maps(dock_ctx *ctx, const dock_grids *g, const dock_ligand *l);
-int evaluator_smem_ok(dock_ctx *ctx, const WarpLayout &w, int warps);
+int evaluator_smem_ok(dock_ctx *ctx, const EvalLayout &w, int warps);
 
 // Kernel launchers (defined in the .cu files).
 cudaError_t launch_relayout(const GridDev &g, float4 *cells, cudaStream_t s);

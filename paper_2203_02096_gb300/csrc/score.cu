@@ -9,17 +9,18 @@ constexpr int kScoreWarps = 4;  // warps per block of the batched evaluators
 template <bool GRAD>
 __global__ void __launch_bounds__(kScoreWarps * 32)
 score_kernel(LigandDev L, GridDev G, const float *__restrict__ geno, int B, float *__restrict__ E,
-             float *__restrict__ grad, WarpLayout W) {
+             float *__restrict__ grad, EvalLayout W) {
     extern __shared__ float4 smem4[];
     float *ws = reinterpret_cast<float *>(smem4) + (threadIdx.x >> 5) * W.total;
     const int lane = threadIdx.x & 31;
+    const dev::Team<1> tm(lane);
     const int nw = gridDim.x * (blockDim.x >> 5);
     const int Gn = L.n_genes;
     for (int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); b < B; b += nw) {
         const float *gb = geno + (size_t)b * Gn;
         for (int j = lane; j < Gn; j += 32) ws[W.geno + j] = gb[j];
         __syncwarp();
-        const float e = dev::eval_warp<GRAD>(L, G, ws, W, lane);
+        const float e = dev::eval_team<1, GRAD>(L, G, ws, W, tm);
         if (lane == 0) E[b] = e;
         if (GRAD)
             for (int j = lane; j < Gn; j += 32) grad[(size_t)b * Gn + j] = ws[W.grad + j];
@@ -30,7 +31,7 @@ score_kernel(LigandDev L, GridDev G, const float *__restrict__ geno, int B, floa
 // Pose only: the forward kinematics of the evaluator, written out per atom
 // in input order (x = t + d).
 __global__ void __launch_bounds__(kScoreWarps * 32)
-pose_kernel(LigandDev L, const float *__restrict__ geno, int B, float *__restrict__ xyz, WarpLayout W) {
+pose_kernel(LigandDev L, const float *__restrict__ geno, int B, float *__restrict__ xyz, EvalLayout W) {
     extern __shared__ float4 smem4[];
     float *ws = reinterpret_cast<float *>(smem4) + (threadIdx.x >> 5) * W.total;
     const int lane = threadIdx.x & 31;
@@ -118,7 +119,7 @@ cudaError_t launch_warps(dock_ctx *ctx, K kernel, int B, int wpb, size_t smem, c
 }
 
 // Warps per block: four when their scratch fits in shared memory, else fewer.
-int pick_warps(dock_ctx *ctx, const WarpLayout &W) {
+int pick_warps(dock_ctx *ctx, const EvalLayout &W) {
     for (int w = kScoreWarps; w > 1; w >>= 1)
         if (evaluator_smem_ok(ctx, W, w)) return w;
     return 1;
@@ -129,7 +130,7 @@ int pick_warps(dock_ctx *ctx, const WarpLayout &W) {
 cudaError_t launch_score(dock_ctx *ctx, const LigandDev &L, const GridDev &G, const float *geno, int B, float *E,
                          float *grad, cudaStream_t s) {
     const bool g = grad != nullptr;
-    WarpLayout W = warp_layout(L.n_atoms, L.n_frag, L.n_pairs, g);
+    EvalLayout W = eval_layout(L.n_atoms, L.n_frag, L.n_pairs, g);
     const int wpb = pick_warps(ctx, W);
     const size_t smem = (size_t)W.total * sizeof(float) * wpb;
     LigandDev l = L;
@@ -142,7 +143,7 @@ cudaError_t launch_score(dock_ctx *ctx, const LigandDev &L, const GridDev &G, co
 }
 
 cudaError_t launch_pose(dock_ctx *ctx, const LigandDev &L, const float *geno, int B, float *xyz, cudaStream_t s) {
-    WarpLayout W = warp_layout(L.n_atoms, L.n_frag, L.n_pairs, false);
+    EvalLayout W = eval_layout(L.n_atoms, L.n_frag, L.n_pairs, false);
     const int wpb = pick_warps(ctx, W);
     const size_t smem = (size_t)W.total * sizeof(float) * wpb;
     LigandDev l = L;
@@ -152,7 +153,7 @@ cudaError_t launch_pose(dock_ctx *ctx, const LigandDev &L, const float *geno, in
     return launch_warps(ctx, pose_kernel, B, wpb, smem, s, "pose", args);
 }
 
-int evaluator_smem_ok(dock_ctx *ctx, const WarpLayout &w, int warps) {
+int evaluator_smem_ok(dock_ctx *ctx, const EvalLayout &w, int warps) {
     return (size_t)w.total * sizeof(float) * warps <= ctx->smem_optin;
 }
 

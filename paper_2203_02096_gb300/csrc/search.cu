@@ -138,10 +138,11 @@ __device__ __forceinline__ int tournament(const float *E, int pop, float p_tour,
 
 template <bool EVAL>
 __global__ void __launch_bounds__(128)
-init_kernel(LigandDev L, GridDev G, GaConst C, float *pop_out, float *E_out, unsigned long long *evals, WarpLayout W) {
+init_kernel(LigandDev L, GridDev G, GaConst C, float *pop_out, float *E_out, unsigned long long *evals, EvalLayout W) {
     extern __shared__ float4 smem4[];
     float *ws = reinterpret_cast<float *>(smem4) + (threadIdx.x >> 5) * W.total;
     const int lane = threadIdx.x & 31;
+    const dev::Team<1> tm(lane);
     const int item = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (item >= C.nruns * C.pop) return;
     const int r = item / C.pop, s = item % C.pop, Gn = 7 + C.nt;
@@ -150,7 +151,7 @@ init_kernel(LigandDev L, GridDev G, GaConst C, float *pop_out, float *E_out, uns
     float *out = pop_out + (size_t)item * Gn;
     for (int j = lane; j < Gn; j += 32) out[j] = ws[W.geno + j];
     if (EVAL) {
-        const float e = dev::eval_warp<false>(L, G, ws, W, lane);
+        const float e = dev::eval_team<1, false>(L, G, ws, W, tm);
         if (lane == 0) {
             E_out[item] = e;
             if (s == 0) atomicAdd(evals + r, (unsigned long long)C.pop);
@@ -163,10 +164,11 @@ template <bool EVAL>
 __global__ void __launch_bounds__(128)
 ga_kernel(LigandDev L, GridDev G, GaConst C, uint32_t gen, const float *__restrict__ pop_old,
           const float *__restrict__ E_old, float *__restrict__ pop_new, float *__restrict__ E_new,
-          long long *info, unsigned long long *evals, WarpLayout W) {
+          long long *info, unsigned long long *evals, EvalLayout W) {
     extern __shared__ float4 smem4[];
     float *ws = reinterpret_cast<float *>(smem4) + (threadIdx.x >> 5) * W.total;
     const int lane = threadIdx.x & 31;
+    const dev::Team<1> tm(lane);
     const int item = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (item >= C.nruns * C.pop) return;
     const int r = item / C.pop, s = item % C.pop, Gn = 7 + C.nt, nblk = 4 + C.nt;
@@ -249,7 +251,7 @@ ga_kernel(LigandDev L, GridDev G, GaConst C, uint32_t gen, const float *__restri
         o[0] = p1; o[1] = p2; o[2] = lo; o[3] = hi; o[4] = (long long)mask;
     }
     if (EVAL) {
-        const float e = dev::eval_warp<false>(L, G, ws, W, lane);
+        const float e = dev::eval_team<1, false>(L, G, ws, W, tm);
         if (lane == 0) E_new[item] = e;
     }
 }
@@ -290,19 +292,22 @@ __device__ __forceinline__ float wrap_any(float x) {
     return x - kTwoPiF * floorf((x + kPiF) * (1.f / kTwoPiF));
 }
 
-// ADADELTA local search, one warp per chain.  With picks (inside dock):
-// chain c is pick c % n_ls of run c / n_ls, updated in place in the
-// population; without: chain c starts at x_in[c] and writes x_out[c].
-__global__ void __launch_bounds__(128)
+// ADADELTA local search, one team of W warps per chain (W = 1: several
+// one-warp teams per block; W > 1: the block is the team).  With picks
+// (inside dock): chain c is pick c % n_ls of run c / n_ls, updated in place
+// in the population; without: chain c starts at x_in[c] and writes x_out[c].
+template <int W>
+__global__ void __launch_bounds__(W == 1 ? 128 : 32 * W)
 ls_kernel(LigandDev L, GridDev G, float *x_in, float *E_pop, const int *__restrict__ picks, int pop, int n_ls,
           int nchains, int iters, float rho, float eps, float *x_out, float *E_out, unsigned long long *evals,
-          WarpLayout W) {
+          EvalLayout Y) {
     extern __shared__ float4 smem4[];
-    float *ws = reinterpret_cast<float *>(smem4) + (threadIdx.x >> 5) * W.total;
-    const int lane = threadIdx.x & 31;
-    const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (c >= nchains) return;
-    const int Gn = L.n_genes;
+    const int team_in_block = W == 1 ? (threadIdx.x >> 5) : 0;
+    float *ws = reinterpret_cast<float *>(smem4) + team_in_block * Y.total;
+    const dev::Team<W> tm(W == 1 ? (threadIdx.x & 31) : threadIdx.x);
+    const int c = W == 1 ? blockIdx.x * (blockDim.x >> 5) + team_in_block : blockIdx.x;
+    if (c >= nchains) return;  // uniform over the team
+    const int Gn = L.n_genes, S = dev::Team<W>::kSize;
     float *xi, *xo, *eo;
     int run = 0;
     if (picks) {
@@ -316,37 +321,41 @@ ls_kernel(LigandDev L, GridDev G, float *x_in, float *E_pop, const int *__restri
         xo = x_out + (size_t)c * Gn;
         eo = E_out + c;
     }
-    const int j0 = lane, j1 = lane + 32;
+    // thread r owns genes r and r + S (the second only when S = 32)
+    const int j0 = tm.rank, j1 = tm.rank + S;
     float x0 = j0 < Gn ? xi[j0] : 0.f, x1 = j1 < Gn ? xi[j1] : 0.f;
     float b0 = x0, b1 = x1, best = INFINITY;
     float g2a = 0.f, g2b = 0.f, d2a = 0.f, d2b = 0.f;
     for (int it = 0; it < iters; ++it) {
-        if (j0 < Gn) ws[W.geno + j0] = x0;
-        if (j1 < Gn) ws[W.geno + j1] = x1;
-        __syncwarp();
-        const float e = dev::eval_warp<true>(L, G, ws, W, lane);
+        if (j0 < Gn) ws[Y.geno + j0] = x0;
+        if (j1 < Gn) ws[Y.geno + j1] = x1;
+        tm.sync();
+        const float e = dev::eval_team<W, true>(L, G, ws, Y, tm);
         if (e < best) {
             best = e;
             b0 = x0;
             b1 = x1;
         }
         if (j0 < Gn) {
-            adadelta(x0, ws[W.grad + j0], g2a, d2a, rho, eps);
+            adadelta(x0, ws[Y.grad + j0], g2a, d2a, rho, eps);
             if (j0 >= 7) x0 = wrap_any(x0);
         }
         if (j1 < Gn) {
-            adadelta(x1, ws[W.grad + j1], g2b, d2b, rho, eps);
+            adadelta(x1, ws[Y.grad + j1], g2b, d2b, rho, eps);
             x1 = wrap_any(x1);
         }
-        __syncwarp();
+        tm.sync();
     }
-    const float q3 = __shfl_sync(0xffffffffu, b0, 3), q4 = __shfl_sync(0xffffffffu, b0, 4);
-    const float q5 = __shfl_sync(0xffffffffu, b0, 5), q6 = __shfl_sync(0xffffffffu, b0, 6);
+    // best point, quaternion normalised (FP32, fixed order)
+    if (j0 < Gn) ws[Y.geno + j0] = b0;
+    if (j1 < Gn) ws[Y.geno + j1] = b1;
+    tm.sync();
+    const float q3 = ws[Y.geno + 3], q4 = ws[Y.geno + 4], q5 = ws[Y.geno + 5], q6 = ws[Y.geno + 6];
     const float n = sqrtf(((q3 * q3 + q4 * q4) + q5 * q5) + q6 * q6);
-    if (lane >= 3 && lane < 7 && n > 0.f) b0 = b0 / n;
+    if (j0 >= 3 && j0 < 7 && n > 0.f) b0 = b0 / n;
     if (j0 < Gn) xo[j0] = b0;
     if (j1 < Gn) xo[j1] = b1;
-    if (lane == 0) {
+    if (tm.rank == 0) {
         *eo = best;
         if (evals) atomicAdd(evals + run, (unsigned long long)iters);
     }
@@ -425,15 +434,54 @@ int resolve_params(dock_ctx *ctx, const dock_params *in, dock_params &p) {
     if (in) p = *in;
     else dock_default_params(&p);
     if (p.ls_count < 0) p.ls_count = (6 * p.pop_size + 99) / 100;
+    if (p.ls_threads != 0 && p.ls_threads != 32 && p.ls_threads != 64 && p.ls_threads != 128 && p.ls_threads != 256)
+        return set_err(ctx, DOCK_ERR_INVALID, "ls_threads must be 0, 32, 64, 128 or 256");
     if (p.pop_size < 2 || p.pop_size > (1 << 20) || p.nruns < 1 || p.max_evals < 0 || p.ls_count > p.pop_size ||
         p.ls_count > kMaxLs || p.ls_iters < 0 || !(p.rho >= 0.f && p.rho < 1.f) || !(p.eps > 0.f))
         return set_err(ctx, DOCK_ERR_INVALID, "invalid dock_params");
     return DOCK_OK;
 }
 
-// LS chains per block: one warp per block while chains are few (spreads them
-// over all SMs), four once there are several per SM.
-int ls_warps(const dock_ctx *ctx, int chains) { return chains >= 8 * ctx->num_sms ? 4 : 1; }
+// Warps per local-search chain: threads_req (32..256) when given, else
+// enough to put about 16 warps on every SM while chains are few.
+int ls_team_warps(const dock_ctx *ctx, int chains, int threads_req) {
+    int w = 1;
+    if (threads_req > 0) {
+        w = threads_req / 32;
+    } else {
+        const long long target = 16LL * ctx->num_sms;
+        while (w < 8 && (long long)chains * 2 * w <= target) w <<= 1;
+    }
+    return w >= 8 ? 8 : w >= 4 ? 4 : w >= 2 ? 2 : 1;
+}
+
+// Launches ls_kernel<W>.  W = 1: four one-warp teams per block once the
+// chains cover every SM several times, else one; W > 1: one team per block.
+cudaError_t launch_ls(dock_ctx *ctx, int W, int chains, const EvalLayout &Y, cudaStream_t s, const char *name,
+                      void **args) {
+    if (chains <= 0) return cudaSuccess;
+    if (W == 1) {
+        const int wpb = chains >= 8 * ctx->num_sms && evaluator_smem_ok(ctx, Y, 4) ? 4 : 1;
+        return launch_items(ctx, ls_kernel<1>, chains, wpb, (size_t)Y.total * 4 * wpb, s, name, args);
+    }
+    const size_t smem = (size_t)Y.total * 4;
+    // one team per block: launch_items with "warps per item" = W
+    auto go = [&](auto kernel) {
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        TimedLaunch tl;
+        timing_begin(ctx, kernel_id(ctx, name), s, &tl);
+        cudaError_t e = cudaLaunchKernel((const void *)kernel, dim3(chains), dim3(32 * W), args, smem, s);
+        timing_end(ctx, s, &tl);
+        ++ctx->launches;
+        return e;
+    };
+    if (W == 2) return go(ls_kernel<2>);
+    if (W == 4) return go(ls_kernel<4>);
+    return go(ls_kernel<8>);
+}
 
 }  // namespace
 
@@ -450,8 +498,8 @@ int dock_async(dock_ctx *ctx, const dock_grids *grids, const dock_ligand *lig, c
     const LigandDev &L = lig->dev;
     const GridDev &G = grids->dev;
     const int Gn = L.n_genes, pop = P.pop_size, R = P.nruns, nls = P.ls_count;
-    const WarpLayout Wn = warp_layout(L.n_atoms, L.n_frag, L.n_pairs, false);
-    const WarpLayout Wg = warp_layout(L.n_atoms, L.n_frag, L.n_pairs, true);
+    const EvalLayout Wn = eval_layout(L.n_atoms, L.n_frag, L.n_pairs, false);
+    const EvalLayout Wg = eval_layout(L.n_atoms, L.n_frag, L.n_pairs, true);
     if (!evaluator_smem_ok(ctx, Wg, 1)) return set_err(ctx, DOCK_ERR_SIZE, "ligand too large for shared memory");
     const int gw = evaluator_smem_ok(ctx, Wn, 4) ? 4 : 1;
     const size_t items = (size_t)R * pop;
@@ -469,7 +517,7 @@ int dock_async(dock_ctx *ctx, const dock_grids *grids, const dock_ligand *lig, c
         GaConst C = ga_const(P, L.n_tors, R, seed);
         LigandDev l = L;
         GridDev g = G;
-        WarpLayout wn = Wn, wg = Wg;
+        EvalLayout wn = Wn, wg = Wg;
         e = cudaMemsetAsync(ev, 0, (size_t)R * 8, s);
         {
             void *a[] = {&l, &g, &C, &popA, &EA, &ev, &wn};
@@ -478,7 +526,7 @@ int dock_async(dock_ctx *ctx, const dock_grids *grids, const dock_ligand *lig, c
         const long long per_gen = (long long)(pop - 1) + (long long)nls * P.ls_iters;
         long long ngen = 0;
         if (P.max_evals > pop) ngen = (P.max_evals - pop + per_gen - 1) / per_gen;
-        const int chains = R * nls, lw = ls_warps(ctx, chains);
+        const int chains = R * nls, lw = ls_team_warps(ctx, chains, P.ls_threads);
         long long *no_info = nullptr;
         float *no_out = nullptr;
         for (long long gen = 1; gen <= ngen && !e; ++gen) {
@@ -496,7 +544,7 @@ int dock_async(dock_ctx *ctx, const dock_grids *grids, const dock_ligand *lig, c
                 float rho = P.rho, eps = P.eps;
                 int nl = nls, ch = chains, popn = pop;
                 void *c[] = {&l, &g, &popB, &EB, &picks, &popn, &nl, &ch, &iters, &rho, &eps, &no_out, &no_out, &ev, &wg};
-                if (!e) e = launch_items(ctx, ls_kernel, chains, lw, (size_t)Wg.total * 4 * lw, s, "dock_ls", c);
+                if (!e) e = launch_ls(ctx, lw, chains, Wg, s, "dock_ls", c);
             }
             std::swap(popA, popB);
             std::swap(EA, EB);
@@ -566,7 +614,7 @@ int dock_init_population(dock_ctx *ctx, const dock_grids *grids, int n_torsions,
     GaConst C = ga_const(P, n_torsions, nruns, seed);
     LigandDev l{};
     GridDev g = grids->dev;
-    WarpLayout w = warp_layout(1, 1, 0, false);
+    EvalLayout w = eval_layout(1, 1, 0, false);
     float *no_e = nullptr;
     unsigned long long *no_ev = nullptr;
     void *a[] = {&l, &g, &C, &pop_out, &no_e, &no_ev, &w};
@@ -588,7 +636,7 @@ int dock_ga_children(dock_ctx *ctx, int n_torsions, int pop, int nruns, const fl
     GaConst C = ga_const(P, n_torsions, nruns, seed);
     LigandDev l{};
     GridDev g{};
-    WarpLayout w = warp_layout(1, 1, 0, false);
+    EvalLayout w = eval_layout(1, 1, 0, false);
     float *no_e = nullptr;
     unsigned long long *no_ev = nullptr;
     long long *inf = (long long *)info;
@@ -611,7 +659,7 @@ int dock_ls_picks(dock_ctx *ctx, int pop, int n_ls, int nruns, uint64_t seed, ui
 }
 
 int dock_local_search(dock_ctx *ctx, const dock_grids *grids, const dock_ligand *lig, const float *x0, int B,
-                      int iters, float rho, float eps, float *x_best, float *E_best, void *stream) {
+                      int iters, float rho, float eps, int threads, float *x_best, float *E_best, void *stream) {
     if (!ctx || !grids || !lig || (B > 0 && (!x0 || !x_best || !E_best)) || B < 0 || iters < 1 ||
         !(rho >= 0.f && rho < 1.f) || !(eps > 0.f))
         return ctx ? set_err(ctx, DOCK_ERR_INVALID, "invalid argument") : DOCK_ERR_INVALID;
@@ -619,9 +667,11 @@ int dock_local_search(dock_ctx *ctx, const dock_grids *grids, const dock_ligand 
     if (rc) return rc;
     if (B == 0) return DOCK_OK;
     const LigandDev &L = lig->dev;
-    WarpLayout W = warp_layout(L.n_atoms, L.n_frag, L.n_pairs, true);
+    EvalLayout W = eval_layout(L.n_atoms, L.n_frag, L.n_pairs, true);
     if (!evaluator_smem_ok(ctx, W, 1)) return set_err(ctx, DOCK_ERR_SIZE, "ligand too large for shared memory");
-    const int lw = ls_warps(ctx, B) == 4 && evaluator_smem_ok(ctx, W, 4) ? 4 : 1;
+    if (threads != 0 && threads != 32 && threads != 64 && threads != 128 && threads != 256)
+        return set_err(ctx, DOCK_ERR_INVALID, "threads must be 0, 32, 64, 128 or 256");
+    const int lw = ls_team_warps(ctx, B, threads);
     LigandDev l = L;
     GridDev g = grids->dev;
     float *xin = const_cast<float *>(x0);
@@ -630,7 +680,7 @@ int dock_local_search(dock_ctx *ctx, const dock_grids *grids, const dock_ligand 
     unsigned long long *no_ev = nullptr;
     int zero = 0, one = 1;
     void *a[] = {&l, &g, &xin, &no_pop, &no_picks, &zero, &one, &B, &iters, &rho, &eps, &x_best, &E_best, &no_ev, &W};
-    cudaError_t e = launch_items(ctx, ls_kernel, B, lw, (size_t)W.total * 4 * lw, (cudaStream_t)stream, "local_search", a);
+    cudaError_t e = launch_ls(ctx, lw, B, W, (cudaStream_t)stream, "local_search", a);
     return e ? cuda_err(ctx, e, "local search kernel") : DOCK_OK;
 }
 
