@@ -298,6 +298,8 @@ def run(args):
     e2e_s = max_over_ranks(time.perf_counter() - t0, dev)
     e2e_value = sum_over_ranks(float(e2e_evals), dev) / e2e_s
 
+    batch = score_grad_throughput(ctx, G, w.box, dev) if not args.no_batch else None
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         v, cores, desc, _ = cpu_sample(w, args.cpu_seconds)
@@ -324,6 +326,7 @@ def run(args):
             "gpu_launches": int(launches),
             "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
             "cpu_baseline": cpu,
+            "score_grad_batch": batch,
             "best_energy_median": float(np.median(out["best_E"].cpu().numpy())),
         }
         print(json.dumps(line), flush=True)
@@ -333,6 +336,44 @@ def run(args):
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def score_grad_throughput(ctx, G, box, dev, reps: int = 5):
+    """score_grad_batch over 65536 random genotypes of a 64-atom / 16-torsion
+    ligand in the same grids (the differentiation workload): evals/s and the
+    FP32 roofline of that kernel (inputs resident, L2 flushed between calls)."""
+    import torch
+
+    from paper_2203_02096_gb300 import capi, synth
+    lig = synth.make_ligand(64, 16, seed=0)
+    L = capi.ligand_from(ctx, lig)
+    genos = torch.from_numpy(synth.make_genotypes(65536, lig.n_torsions, box, seed=0)).to(dev)
+    E = torch.empty(65536, device=dev)
+    grad = torch.empty_like(genos)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    for _ in range(3):
+        capi.score_grad_batch(ctx, G, L, genos, E, grad)
+    ms = []
+    for k in range(reps):
+        flush.fill_(float(k))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        capi.score_grad_batch(ctx, G, L, genos, E, grad)
+        b.record()
+        torch.cuda.synchronize(dev)
+        ms.append(a.elapsed_time(b))
+    xyz = capi.pose_batch(ctx, L, genos[:1024]).cpu().numpy()
+    pij = pair_list(lig)
+    d = np.linalg.norm(xyz[:, pij[:, 0]] - xyz[:, pij[:, 1]], axis=2)
+    p_in = float((d < 8.0).sum(axis=1).mean())
+    f = flops_score_grad(lig.n_atoms, lig.n_torsions, len(pij), p_in)
+    t = float(np.mean(ms)) / 1e3
+    L.free()
+    achieved = f * 65536 / t / 1e12
+    return {"workload": "65536 genotypes, 64 atoms / 16 torsions, 64^3 x 9 maps", "evals_per_s": 65536 / t,
+            "launch_ms": t * 1e3, "flops_per_eval": f, "achieved_tflops": achieved,
+            "frac_fp32_peak": achieved / peak_fp32_tflops(),
+            "l2_achieved_gbs": grid_bytes_per_eval(lig.n_atoms) * 65536 / t / 1e9}
 
 
 def pair_list(lig):
@@ -388,6 +429,7 @@ def main(argv=None):
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the score_grad_batch side measurement")
     ap.add_argument("--ls-threads", type=int, default=0, help="threads per local-search chain (0 = auto)")
     args = ap.parse_args(argv)
     if args.warmup < 3:

@@ -84,12 +84,21 @@ __device__ __forceinline__ void locate(const GridDev &G, float ux, float uy, flo
     c.cell = (iz * (G.ny - 1) + iy) * (G.nx - 1) + ix;
 }
 
-// Trilinear read of map m in the located cell; derivatives are with respect
-// to the in-cell fractions.
+// The 8 corner values of map m in the located cell (one 32-byte sector).
+struct Cell8 {
+    float4 a, b;
+};
+
+__device__ __forceinline__ Cell8 load_cell(const GridDev &G, int cell, int m) {
+    const float4 *p = G.cells + 2 * ((size_t)cell * G.M + m);
+    return Cell8{ldg(p), ldg(p + 1)};
+}
+
+// Trilinear read in the located cell; derivatives are with respect to the
+// in-cell fractions.
 template <bool GRAD>
-__device__ __forceinline__ float read_map(const GridDev &G, const CellPos &c, int m, float &gx, float &gy, float &gz) {
-    const float4 *p = G.cells + 2 * ((size_t)c.cell * G.M + m);
-    const float4 a = ldg(p), b = ldg(p + 1);
+__device__ __forceinline__ float trilinear(const Cell8 &v, const CellPos &c, float &gx, float &gy, float &gz) {
+    const float4 a = v.a, b = v.b;
     const float ax = a.y - a.x, az = a.w - a.z, bx = b.y - b.x, bz = b.w - b.z;
     const float x00 = fmaf(c.fx, ax, a.x), x10 = fmaf(c.fx, az, a.z);
     const float x01 = fmaf(c.fx, bx, b.x), x11 = fmaf(c.fx, bz, b.z);
@@ -104,25 +113,38 @@ __device__ __forceinline__ float read_map(const GridDev &G, const CellPos &c, in
     return fmaf(c.fz, y1 - y0, y0);
 }
 
-// Energy of one atom (type map + q * electrostatic + |q| * desolvation +
-// out-of-box penalty) and dE/dx.
-template <bool GRAD>
-__device__ __forceinline__ float atom_grid_energy(const GridDev &G, int map_t, float q, float ux, float uy, float uz,
-                                                  float3 &g) {
+// An atom's grid reads, issued before they are needed.
+struct AtomCells {
     CellPos c;
-    locate(G, ux, uy, uz, c);
+    Cell8 t, e, d;
+    float q;
+};
+
+__device__ __forceinline__ void atom_fetch(const GridDev &G, int map_t, float q, float ux, float uy, float uz,
+                                           AtomCells &A) {
+    locate(G, ux, uy, uz, A.c);
+    A.t = load_cell(G, A.c.cell, map_t);
+    A.e = load_cell(G, A.c.cell, G.emap);
+    A.d = load_cell(G, A.c.cell, G.dmap);
+    A.q = q;
+}
+
+// Energy of one atom (type map + q * electrostatic + |q| * desolvation +
+// out-of-box penalty) and dE/dx, from its fetched cells.
+template <bool GRAD>
+__device__ __forceinline__ float atom_grid_energy(const GridDev &G, const AtomCells &A, float3 &g) {
     float tx, ty, tz, ex, ey, ez, dx, dy, dz;
-    const float aq = fabsf(q);
-    const float vt = read_map<GRAD>(G, c, map_t, tx, ty, tz);
-    const float ve = read_map<GRAD>(G, c, G.emap, ex, ey, ez);
-    const float vd = read_map<GRAD>(G, c, G.dmap, dx, dy, dz);
+    const float q = A.q, aq = fabsf(q);
+    const float vt = trilinear<GRAD>(A.t, A.c, tx, ty, tz);
+    const float ve = trilinear<GRAD>(A.e, A.c, ex, ey, ez);
+    const float vd = trilinear<GRAD>(A.d, A.c, dx, dy, dz);
     if (GRAD) {
-        const float sx = c.cx ? 0.f : G.inv_h, sy = c.cy ? 0.f : G.inv_h, sz = c.cz ? 0.f : G.inv_h;
-        g.x = fmaf(sx, fmaf(aq, dx, fmaf(q, ex, tx)), c.gpx);
-        g.y = fmaf(sy, fmaf(aq, dy, fmaf(q, ey, ty)), c.gpy);
-        g.z = fmaf(sz, fmaf(aq, dz, fmaf(q, ez, tz)), c.gpz);
+        const float sx = A.c.cx ? 0.f : G.inv_h, sy = A.c.cy ? 0.f : G.inv_h, sz = A.c.cz ? 0.f : G.inv_h;
+        g.x = fmaf(sx, fmaf(aq, dx, fmaf(q, ex, tx)), A.c.gpx);
+        g.y = fmaf(sy, fmaf(aq, dy, fmaf(q, ey, ty)), A.c.gpy);
+        g.z = fmaf(sz, fmaf(aq, dz, fmaf(q, ez, tz)), A.c.gpz);
     }
-    return fmaf(aq, vd, fmaf(q, ve, vt)) + c.pen;
+    return fmaf(aq, vd, fmaf(q, ve, vt)) + A.c.pen;
 }
 
 // Intramolecular pair: energy, and s = (dE/dr)/r (0 below the floor), for
@@ -166,17 +188,21 @@ __device__ __forceinline__ float group_sum(float v, int k) {
 }
 
 // Team-wide sum, same bits on every thread: warp butterflies, then the warps'
-// partials added in warp order.
+// partials added in warp order.  Its barrier also publishes every earlier
+// shared-memory write of the team; `red` is not rewritten before two more
+// team barriers have passed.
 template <int W>
 __device__ __forceinline__ float team_sum(const Team<W> &tm, float v, float *red) {
     v = warp_sum(v);
-    if (W == 1) return v;
+    if (W == 1) {
+        __syncwarp();
+        return v;
+    }
     if (tm.lane() == 0) red[tm.warp()] = v;
     tm.sync();
     float s = red[0];
 #pragma unroll
     for (int w = 1; w < W; ++w) s += red[w];
-    tm.sync();
     return s;
 }
 
@@ -235,43 +261,49 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
         depth = fr.w;
     }
     // Forward kinematics, one tree level at a time: M_child = M_parent o L_k.
-    for (int d = 1; d <= L.max_depth; ++d) {
-        tm.sync();
-        if (r < T && depth == d) {
-            const float4 p0 = M[3 * parent], p1 = M[3 * parent + 1], p2 = M[3 * parent + 2];
-            float4 *o = M + 3 * (r + 1);
-            o[0] = make_float4(p0.x * r00 + p0.y * r10 + p0.z * r20, p0.x * r01 + p0.y * r11 + p0.z * r21,
-                               p0.x * r02 + p0.y * r12 + p0.z * r22, p0.x * t0 + p0.y * t1 + p0.z * t2 + p0.w);
-            o[1] = make_float4(p1.x * r00 + p1.y * r10 + p1.z * r20, p1.x * r01 + p1.y * r11 + p1.z * r21,
-                               p1.x * r02 + p1.y * r12 + p1.z * r22, p1.x * t0 + p1.y * t1 + p1.z * t2 + p1.w);
-            o[2] = make_float4(p2.x * r00 + p2.y * r10 + p2.z * r20, p2.x * r01 + p2.y * r11 + p2.z * r21,
-                               p2.x * r02 + p2.y * r12 + p2.z * r22, p2.x * t0 + p2.y * t1 + p2.z * t2 + p2.w);
+    // Torsions are threads 0..T-1 < 32, all in warp 0.
+    if (tm.warp() == 0) {
+        for (int d = 1; d <= L.max_depth; ++d) {
+            __syncwarp();
+            if (r < T && depth == d) {
+                const float4 p0 = M[3 * parent], p1 = M[3 * parent + 1], p2 = M[3 * parent + 2];
+                float4 *o = M + 3 * (r + 1);
+                o[0] = make_float4(p0.x * r00 + p0.y * r10 + p0.z * r20, p0.x * r01 + p0.y * r11 + p0.z * r21,
+                                   p0.x * r02 + p0.y * r12 + p0.z * r22, p0.x * t0 + p0.y * t1 + p0.z * t2 + p0.w);
+                o[1] = make_float4(p1.x * r00 + p1.y * r10 + p1.z * r20, p1.x * r01 + p1.y * r11 + p1.z * r21,
+                                   p1.x * r02 + p1.y * r12 + p1.z * r22, p1.x * t0 + p1.y * t1 + p1.z * t2 + p1.w);
+                o[2] = make_float4(p2.x * r00 + p2.y * r10 + p2.z * r20, p2.x * r01 + p2.y * r11 + p2.z * r21,
+                                   p2.x * r02 + p2.y * r12 + p2.z * r22, p2.x * t0 + p2.y * t1 + p2.z * t2 + p2.w);
+            }
         }
     }
     tm.sync();
 
-    // Atoms: position, then the particle-grid term.
-    const float tux = (tx - G.ox) * G.inv_h, tuy = (ty - G.oy) * G.inv_h, tuz = (tz - G.oz) * G.inv_h;
-    float4 *Fv = reinterpret_cast<float4 *>(ws + Y.f);
-    float e = 0.f;
+    // Atom positions (relative to t).
     for (int i = r; i < N; i += S) {
         const float4 p = ldg(L.ref + i);
-        const int meta = ldg(L.meta + i);
-        const int f = meta >> 8;
+        const int f = ldg(L.meta + i) >> 8;
         const float4 m0 = M[3 * f], m1 = M[3 * f + 1], m2 = M[3 * f + 2];
-        const float dx = fmaf(m0.x, p.x, fmaf(m0.y, p.y, fmaf(m0.z, p.z, m0.w)));
-        const float dy = fmaf(m1.x, p.x, fmaf(m1.y, p.y, fmaf(m1.z, p.z, m1.w)));
-        const float dz = fmaf(m2.x, p.x, fmaf(m2.y, p.y, fmaf(m2.z, p.z, m2.w)));
-        X[i] = make_float4(dx, dy, dz, 0.f);
-        float3 g;
-        e += atom_grid_energy<GRAD>(G, ldg(G.map_of_type + (meta & 255)), p.w, fmaf(dx, G.inv_h, tux),
-                                    fmaf(dy, G.inv_h, tuy), fmaf(dz, G.inv_h, tuz), g);
-        if (GRAD) Fv[i] = make_float4(g.x, g.y, g.z, 0.f);
+        X[i] = make_float4(fmaf(m0.x, p.x, fmaf(m0.y, p.y, fmaf(m0.z, p.z, m0.w))),
+                           fmaf(m1.x, p.x, fmaf(m1.y, p.y, fmaf(m1.z, p.z, m1.w))),
+                           fmaf(m2.x, p.x, fmaf(m2.y, p.y, fmaf(m2.z, p.z, m2.w))), 0.f);
     }
     tm.sync();
 
+    // Particle-grid reads of the thread's first atom go out first; the pair
+    // loop runs while they are in flight.
+    const float tux = (tx - G.ox) * G.inv_h, tuy = (ty - G.oy) * G.inv_h, tuz = (tz - G.oz) * G.inv_h;
+    float4 *Fv = reinterpret_cast<float4 *>(ws + Y.f);
+    AtomCells A0;
+    if (r < N) {
+        const float4 xi = X[r];
+        atom_fetch(G, ldg(G.map_of_type + (ldg(L.meta + r) & 255)), ldg(L.ref + r).w, fmaf(xi.x, G.inv_h, tux),
+                   fmaf(xi.y, G.inv_h, tuy), fmaf(xi.z, G.inv_h, tuz), A0);
+    }
     // Intramolecular pairs, strided over the team; s_p = (dE/dr)/r kept per pair.
+    float e = 0.f;
     float *Sp = ws + Y.s;
+#pragma unroll 2
     for (int p = r; p < P; p += S) {
         const uint32_t ij = ldg(L.pair_ij + p);
         const float4 xi = X[ij & 0xffffu], xj = X[ij >> 16];
@@ -280,6 +312,16 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
         float s = 0.f;
         if (r2 < kCut2) e += pair_energy<GRAD>(r2, ldg(L.pair_c + p), ldg(L.pair_ds + p), s);
         if (GRAD) Sp[p] = s;
+    }
+    for (int i = r; i < N; i += S) {
+        if (i != r) {
+            const float4 xi = X[i];
+            atom_fetch(G, ldg(G.map_of_type + (ldg(L.meta + i) & 255)), ldg(L.ref + i).w, fmaf(xi.x, G.inv_h, tux),
+                       fmaf(xi.y, G.inv_h, tuy), fmaf(xi.z, G.inv_h, tuz), A0);
+        }
+        float3 g;
+        e += atom_grid_energy<GRAD>(G, A0, g);
+        if (GRAD) Fv[i] = make_float4(g.x, g.y, g.z, 0.f);
     }
     if (!GRAD) return team_sum(tm, e, red);
     tm.sync();
@@ -320,9 +362,39 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
     }
     tm.sync();
 
-    // Gradient: range k < T is the contiguous atom range torsion k moves,
-    // range T is the whole ligand (translation and rotation).  Each range is
-    // summed by m lanes and a butterfly.
+    // Per-fragment sums of f_i and (x_i - t) x f_i (m lanes per fragment).
+    float4 *FS = reinterpret_cast<float4 *>(ws + Y.fs);
+    const int F = L.n_frag;
+    {
+        const int m = lanes_per_item(F, S), per = S / m, sub = r & (m - 1);
+        for (int base = 0; base < F; base += per) {
+            const int f = base + r / m;
+            const bool act = f < F;
+            int lo = 0, hi = 0;
+            if (act) {
+                const int4 fr = ldg(L.frag + f);
+                lo = fr.x;
+                hi = fr.y;
+            }
+            float a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0, a5 = 0;
+            for (int i = lo + sub; i < hi; i += m) {
+                const float4 fv = Fv[i], tq = Tq[i];
+                a0 += fv.x; a1 += fv.y; a2 += fv.z;
+                a3 += tq.x; a4 += tq.y; a5 += tq.z;
+            }
+            a0 = group_sum(a0, m); a1 = group_sum(a1, m); a2 = group_sum(a2, m);
+            a3 = group_sum(a3, m); a4 = group_sum(a4, m); a5 = group_sum(a5, m);
+            if (act && sub == 0) {
+                FS[2 * f] = make_float4(a0, a1, a2, 0.f);
+                FS[2 * f + 1] = make_float4(a3, a4, a5, 0.f);
+            }
+        }
+    }
+    tm.sync();
+
+    // Gradient: range k < T is the fragments torsion k moves (a contiguous
+    // run in depth-first order), range T is all fragments (translation and
+    // rotation); m lanes per range and a butterfly.
     float *grad = ws + Y.grad;
     {
         const int R = T + 1, m = lanes_per_item(R, S), per = S / m, sub = r & (m - 1);
@@ -331,19 +403,14 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
             const bool act = k < R;
             int lo = 0, hi = 0;
             if (act) {
-                if (k < T) {
-                    const int2 rg = ldg(L.tors_range + k);
-                    lo = rg.x;
-                    hi = rg.y;
-                } else {
-                    hi = N;
-                }
+                lo = k < T ? k + 1 : 0;
+                hi = k < T ? ldg(L.sub_end + k + 1) : F;
             }
             float a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0, a5 = 0;
-            for (int i = lo + sub; i < hi; i += m) {
-                const float4 f = Fv[i], t = Tq[i];
-                a0 += f.x; a1 += f.y; a2 += f.z;
-                a3 += t.x; a4 += t.y; a5 += t.z;
+            for (int f = lo + sub; f < hi; f += m) {
+                const float4 u = FS[2 * f], v = FS[2 * f + 1];
+                a0 += u.x; a1 += u.y; a2 += u.z;
+                a3 += v.x; a4 += v.y; a5 += v.z;
             }
             a0 = group_sum(a0, m); a1 = group_sum(a1, m); a2 = group_sum(a2, m);
             a3 = group_sum(a3, m); a4 = group_sum(a4, m); a5 = group_sum(a5, m);
@@ -369,9 +436,7 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
             }
         }
     }
-    e = team_sum(tm, e, red);  // its barriers also publish grad[] (W > 1)
-    tm.sync();
-    return e;
+    return team_sum(tm, e, red);  // its barrier publishes grad[]
 }
 
 }  // namespace dev

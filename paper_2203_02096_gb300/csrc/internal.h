@@ -56,7 +56,7 @@ struct GridDev {
 // Shared-memory scratch of one evaluating team, offsets in floats (each a
 // multiple of 4 so float4 views are aligned).
 struct EvalLayout {
-    int geno, grad, red, M, x, f, tq, s, total;
+    int geno, grad, red, M, fs, x, f, tq, s, total;
 };
 
 __host__ __device__ inline int round4(int v) { return (v + 3) & ~3; }
@@ -68,6 +68,7 @@ __host__ __device__ inline EvalLayout eval_layout(int n_atoms, int n_frag, int n
     w.grad = o; o += 48;
     w.red = o; o += 32;
     w.M = o; o += 12 * n_frag;
+    w.fs = o; o += grad ? 8 * n_frag : 0;
     w.x = o; o += 4 * n_atoms;
     w.f = o; o += grad ? 4 * n_atoms : 0;
     w.tq = o; o += grad ? 4 * n_atoms : 0;

@@ -296,8 +296,9 @@ __device__ __forceinline__ float wrap_any(float x) {
 // one-warp teams per block; W > 1: the block is the team).  With picks
 // (inside dock): chain c is pick c % n_ls of run c / n_ls, updated in place
 // in the population; without: chain c starts at x_in[c] and writes x_out[c].
+// Residency: W = 8 keeps 3 blocks (24 warps) per SM, W = 4 four, W = 2 eight.
 template <int W>
-__global__ void __launch_bounds__(W == 1 ? 128 : 32 * W)
+__global__ void __launch_bounds__(W == 1 ? 128 : 32 * W, W == 8 ? 3 : W == 4 ? 4 : W == 2 ? 8 : 4)
 ls_kernel(LigandDev L, GridDev G, float *x_in, float *E_pop, const int *__restrict__ picks, int pop, int n_ls,
           int nchains, int iters, float rho, float eps, float *x_out, float *E_out, unsigned long long *evals,
           EvalLayout Y) {
@@ -344,7 +345,8 @@ ls_kernel(LigandDev L, GridDev G, float *x_in, float *E_pop, const int *__restri
             adadelta(x1, ws[Y.grad + j1], g2b, d2b, rho, eps);
             x1 = wrap_any(x1);
         }
-        tm.sync();
+        // no barrier needed here: the next writes (genes) touch a region no
+        // thread reads after the evaluator's last barrier
     }
     // best point, quaternion normalised (FP32, fixed order)
     if (j0 < Gn) ws[Y.geno + j0] = b0;
