@@ -175,6 +175,35 @@ int dock(dock_ctx *ctx, const dock_grids *grids, const dock_ligand *lig, const d
 int dock_async(dock_ctx *ctx, const dock_grids *grids, const dock_ligand *lig, const dock_params *params,
                uint64_t seed, float *best_geno, float *best_E32, double *best_E, int64_t *evals_used, void *stream);
 
+/* ---- docking without device allocation ----
+ * Not a step of the paper's method (it has no counterpart there): the same
+ * docking as dock_async -- same kernels, same results for the same inputs --
+ * for callers that must not allocate device memory during the call, such as
+ * a host application that has handed all device memory to its own pool, a
+ * plugin that is only ever given pointers, or a latency-critical loop in
+ * which cudaMalloc/cudaFree (which can synchronise the device) are not
+ * acceptable.  Its working buffers (two populations of nruns x pop_size
+ * genotypes, their energies, the local-search picks and the per-run
+ * counters; plus nruns floats when best_E32 is NULL) come from one fixed
+ * array of DOCK_NOALLOC_SCRATCH_BYTES that every GPU loading the library
+ * holds until the process exits.  It calls no cudaMalloc, cudaFree or
+ * allocating library routine, and never the context's allocator.
+ *  - A request needing more scratch than the array holds (about
+ *    2 * nruns * pop_size * (4*G + 4) bytes) fails with DOCK_ERR_SIZE and a
+ *    message giving the bytes needed.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.  The context's device must be current.
+ *  - All calls share the one array and it keeps the last call's contents
+ *    (the counters are cleared at the start of each call): calls that
+ *    overlap on the GPU -- on different streams, or from different host
+ *    threads -- race on it; serialise them.
+ * Outputs and arguments as dock_async. */
+#define DOCK_NOALLOC_SCRATCH_BYTES (8u << 20)
+int dock_async_noalloc(dock_ctx *ctx, const dock_grids *grids, const dock_ligand *lig, const dock_params *params,
+                       uint64_t seed, float *best_geno, float *best_E32, double *best_E, int64_t *evals_used,
+                       void *stream);
+
 /* ---- operator-level entry points (the steps dock() composes) ---- all
  * pointers device, FP32 genes, runs r = 0..nruns-1 laid out [nruns][pop][G].
  * dock_init_population: generation-0 individuals (translation uniform in

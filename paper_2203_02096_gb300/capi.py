@@ -63,6 +63,7 @@ SIGNATURES = {
     "pose_batch": (_i, [_vp, _vp, _vp, _i, _vp, _vp]),
     "dock": (_i, [_vp, _vp, _vp, _P(DockParams), _u64, _vp, _vp, _vp]),
     "dock_async": (_i, [_vp, _vp, _vp, _P(DockParams), _u64, _vp, _vp, _vp, _vp, _vp]),
+    "dock_async_noalloc": (_i, [_vp, _vp, _vp, _P(DockParams), _u64, _vp, _vp, _vp, _vp, _vp]),
     "dock_init_population": (_i, [_vp, _vp, _i, _i, _i, _u64, _vp, _vp]),
     "dock_ga_children": (_i, [_vp, _i, _i, _i, _vp, _vp, _u64, _u32, _P(DockParams), _vp, _vp, _vp]),
     "dock_ls_picks": (_i, [_vp, _i, _i, _i, _u64, _u32, _vp, _vp]),
@@ -136,9 +137,11 @@ class Context:
         self.device = device
         torch.cuda.set_device(device)
         self._cb = None
+        self.alloc_calls = 0   # device allocations the library asked for
         alloc = None
         if use_torch_allocator:
             def _alloc(nbytes, stream, user):
+                self.alloc_calls += 1
                 try:
                     return torch.cuda.caching_allocator_alloc(int(nbytes), device, stream=int(stream or 0))
                 except Exception:  # reported to the caller as DOCK_ERR_OOM
@@ -315,6 +318,16 @@ def dock_async(ctx: Context, grids: Grids, lig: Ligand, params: DockParams, seed
     ctx.check(ctx.lib.dock_async(ctx.h, grids.h, lig.h, C.byref(params), int(seed), _ptr(out["best_geno"]),
                                  _ptr(out["best_E32"]), _ptr(out["best_E"]), _ptr(out["evals"]), _stream(stream)),
               "dock_async")
+    return out
+
+
+def dock_async_noalloc(ctx: Context, grids: Grids, lig: Ligand, params: DockParams, seed: int, out, stream=None):
+    """dock_async with its working buffers in the library's fixed device array
+    (no device allocation in the call); ``out`` holds caller-owned tensors
+    best_geno, best_E32, best_E, evals as returned by dock_async."""
+    ctx.check(ctx.lib.dock_async_noalloc(ctx.h, grids.h, lig.h, C.byref(params), int(seed), _ptr(out["best_geno"]),
+                                         _ptr(out["best_E32"]), _ptr(out["best_E"]), _ptr(out["evals"]),
+                                         _stream(stream)), "dock_async_noalloc")
     return out
 
 

@@ -12,6 +12,8 @@
 #include <math.h>
 
 #include <algorithm>
+#include <mutex>
+#include <string>
 
 #include "eval.cuh"
 
@@ -697,3 +699,123 @@ int dock_philox(dock_ctx *ctx, const uint32_t *ctr, int n, uint32_t key_lo, uint
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// dock_async_noalloc: the docking of dock_async with its working buffers
+// (two populations, their energies, the local-search picks and the per-run
+// evaluation counters) carved out of one fixed device array instead of
+// allocated memory.
+
+namespace {
+
+// Module-scope scratch: every device that loads the library holds one copy
+// until the process exits.
+__device__ __align__(256) unsigned char g_noalloc_scratch[DOCK_NOALLOC_SCRATCH_BYTES];
+
+// Device address of the array on each device, looked up once per device
+// with that device current (the host-side name is only a stand-in).
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[128] = {};
+
+int noalloc_base(dock_ctx *ctx, unsigned char **base) {
+    int cur = -1;
+    cudaError_t e = cudaGetDevice(&cur);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "cudaGetDevice");
+    if (cur != ctx->device || cur < 0 || cur >= 128)
+        return set_err(ctx, DOCK_ERR_INVALID, "the context's device must be the current device");
+    std::lock_guard<std::mutex> g(g_noalloc_mu);
+    if (!g_noalloc_ptr[cur]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) return cuda_err(ctx, e == cudaSuccess ? cudaErrorInvalidSymbol : e, "cudaGetSymbolAddress");
+        g_noalloc_ptr[cur] = p;
+    }
+    *base = (unsigned char *)g_noalloc_ptr[cur];
+    return DOCK_OK;
+}
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+}  // namespace
+
+extern "C" int dock_async_noalloc(dock_ctx *ctx, const dock_grids *grids, const dock_ligand *lig,
+                                  const dock_params *params, uint64_t seed, float *best_geno, float *best_E32,
+                                  double *best_E, int64_t *evals_used, void *stream) {
+    if (!ctx || !grids || !lig || !best_geno) return ctx ? set_err(ctx, DOCK_ERR_INVALID, "null argument") : DOCK_ERR_INVALID;
+    dock_params P;
+    int rc = resolve_params(ctx, params, P);
+    if (rc) return rc;
+    if ((rc = check_maps(ctx, grids, lig))) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    const LigandDev &L = lig->dev;
+    const GridDev &G = grids->dev;
+    const int Gn = L.n_genes, pop = P.pop_size, R = P.nruns, nls = P.ls_count;
+    const EvalLayout Wn = eval_layout(L.n_atoms, L.n_frag, L.n_pairs, false);
+    const EvalLayout Wg = eval_layout(L.n_atoms, L.n_frag, L.n_pairs, true);
+    if (!evaluator_smem_ok(ctx, Wg, 1)) return set_err(ctx, DOCK_ERR_SIZE, "ligand too large for shared memory");
+    const int gw = evaluator_smem_ok(ctx, Wn, 4) ? 4 : 1;
+    const size_t items = (size_t)R * pop;
+    // carve the scratch: populations, energies, picks, counters, FP32 bests
+    const size_t o_popA = 0, o_popB = o_popA + align256(items * Gn * 4);
+    const size_t o_EA = o_popB + align256(items * Gn * 4), o_EB = o_EA + align256(items * 4);
+    const size_t o_picks = o_EB + align256(items * 4);
+    const size_t o_ev = o_picks + align256((size_t)R * (nls > 0 ? nls : 1) * 4);
+    const size_t o_bE = o_ev + align256((size_t)R * 8);
+    const size_t need = o_bE + (best_E32 ? 0 : align256((size_t)R * 4));
+    if (need > (size_t)DOCK_NOALLOC_SCRATCH_BYTES)
+        return set_err(ctx, DOCK_ERR_SIZE, "dock_async_noalloc needs " + std::to_string(need) +
+                                               " bytes of scratch; its fixed array holds " +
+                                               std::to_string((size_t)DOCK_NOALLOC_SCRATCH_BYTES));
+    unsigned char *base = nullptr;
+    if ((rc = noalloc_base(ctx, &base))) return rc;
+    float *popA = (float *)(base + o_popA), *popB = (float *)(base + o_popB);
+    float *EA = (float *)(base + o_EA), *EB = (float *)(base + o_EB);
+    int *picks = (int *)(base + o_picks);
+    unsigned long long *ev = (unsigned long long *)(base + o_ev);
+    float *bE32 = best_E32 ? best_E32 : (float *)(base + o_bE);
+    GaConst C = ga_const(P, L.n_tors, R, seed);
+    LigandDev l = L;
+    GridDev g = G;
+    EvalLayout wn = Wn, wg = Wg;
+    // the array keeps the previous call's contents: the counters restart at 0
+    cudaError_t e = cudaMemsetAsync(ev, 0, (size_t)R * 8, s);
+    {
+        void *a[] = {&l, &g, &C, &popA, &EA, &ev, &wn};
+        if (!e) e = launch_items(ctx, init_kernel<true>, (int)items, gw, (size_t)Wn.total * 4 * gw, s, "dock_init", a);
+    }
+    const long long per_gen = (long long)(pop - 1) + (long long)nls * P.ls_iters;
+    long long ngen = 0;
+    if (P.max_evals > pop) ngen = (P.max_evals - pop + per_gen - 1) / per_gen;
+    const int chains = R * nls, lw = ls_team_warps(ctx, chains, P.ls_threads);
+    long long *no_info = nullptr;
+    float *no_out = nullptr;
+    for (long long gen = 1; gen <= ngen && !e; ++gen) {
+        uint32_t g32 = (uint32_t)gen;
+        void *a[] = {&l, &g, &C, &g32, &popA, &EA, &popB, &EB, &no_info, &ev, &wn};
+        e = launch_items(ctx, ga_kernel<true>, (int)items, gw, (size_t)Wn.total * 4 * gw, s, "dock_ga", a);
+        if (!e && chains > 0 && P.ls_iters > 0) {
+            picks_kernel<<<(R + 63) / 64, 64, 0, s>>>(pop, nls, R, C.key, g32, picks);
+            ++ctx->launches;
+            e = cudaGetLastError();
+            int iters = P.ls_iters;
+            float rho = P.rho, eps = P.eps;
+            int nl = nls, ch = chains, popn = pop;
+            void *c[] = {&l, &g, &popB, &EB, &picks, &popn, &nl, &ch, &iters, &rho, &eps, &no_out, &no_out, &ev, &wg};
+            if (!e) e = launch_ls(ctx, lw, chains, Wg, s, "dock_ls", c);
+        }
+        std::swap(popA, popB);
+        std::swap(EA, EB);
+    }
+    if (!e) {
+        final_kernel<<<(R + 3) / 4, 128, 0, s>>>(popA, EA, pop, R, Gn, best_geno, bE32);
+        ++ctx->launches;
+        e = cudaGetLastError();
+    }
+    if (!e && best_E) e = launch_rescore64(ctx, L, G, best_geno, R, best_E, s);
+    if (!e && evals_used) {
+        evals_out_kernel<<<(R + 127) / 128, 128, 0, s>>>(ev, R, evals_used);
+        ++ctx->launches;
+        e = cudaGetLastError();
+    }
+    return e ? cuda_err(ctx, e, "dock kernels") : DOCK_OK;
+}
