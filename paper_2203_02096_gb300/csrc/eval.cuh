@@ -213,61 +213,60 @@ __device__ __forceinline__ int lanes_per_item(int items, int team) {
     return k;
 }
 
-// Evaluates the genotype stored at ws[L.geno ...]; returns E on every thread
-// of the team.  With GRAD, dE/dgenotype is left at ws[L.grad ...].
+// Evaluates the genotype stored at ws[Y.geno ...], which only warp 0 needs
+// to have written (and, for W > 1, only warp 0 may have written since the
+// team's previous barrier).  Returns E on every thread of the team; with
+// GRAD, dE/dgenotype is left at ws[Y.grad ...].
 template <int W, bool GRAD>
 __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, const EvalLayout &Y, const Team<W> &tm) {
     constexpr int S = Team<W>::kSize;
-    const int r = tm.rank;
+    const int r = tm.rank, lane = tm.lane();
     const float *geno = ws + Y.geno;
     float4 *M = reinterpret_cast<float4 *>(ws + Y.M);
     float4 *X = reinterpret_cast<float4 *>(ws + Y.x);
+    float4 *PF = reinterpret_cast<float4 *>(ws + Y.pf);
     float *red = ws + Y.red;
-    const int T = L.n_tors, N = L.n_atoms, P = L.n_pairs;
+    const int T = L.n_tors, N = L.n_atoms, NB = L.nb8;
 
-    // Rigid-body part: positions are kept relative to the translation t.
-    const float tx = geno[0], ty = geno[1], tz = geno[2];
-    float qw = geno[3], qx = geno[4], qy = geno[5], qz = geno[6];
-    const float qn2 = qw * qw + qx * qx + qy * qy + qz * qz;
-    float qinv = 0.f;
-    if (qn2 >= 1e-24f) {
-        qinv = rsqrtf(qn2);
-        qw *= qinv; qx *= qinv; qy *= qinv; qz *= qinv;
-    } else {
-        qw = 1.f; qx = qy = qz = 0.f;
-    }
-    if (r == 0) {
-        M[0] = make_float4(1.f - 2.f * (qy * qy + qz * qz), 2.f * (qx * qy - qw * qz), 2.f * (qx * qz + qw * qy), 0.f);
-        M[1] = make_float4(2.f * (qx * qy + qw * qz), 1.f - 2.f * (qx * qx + qz * qz), 2.f * (qy * qz - qw * qx), 0.f);
-        M[2] = make_float4(2.f * (qx * qz - qw * qy), 2.f * (qy * qz + qw * qx), 1.f - 2.f * (qx * qx + qy * qy), 0.f);
-    }
-    // Thread k < T holds the local transform of torsion k: rotation by tau_k
-    // about the reference bond axis through atom b (Rodrigues, right-hand rule).
-    float r00 = 0, r01 = 0, r02 = 0, r10 = 0, r11 = 0, r12 = 0, r20 = 0, r21 = 0, r22 = 0, t0 = 0, t1 = 0, t2 = 0;
-    int depth = 0, parent = 0;
-    if (r < T) {
-        float s, c;
-        sincosf(geno[ldg(L.tors_gene + r)], &s, &c);
-        const float4 u = ldg(L.tors_u + r), b = ldg(L.tors_b + r);
-        const float oc = 1.f - c;
-        r00 = fmaf(oc * u.x, u.x, c);        r01 = fmaf(oc * u.x, u.y, -s * u.z); r02 = fmaf(oc * u.x, u.z, s * u.y);
-        r10 = fmaf(oc * u.y, u.x, s * u.z);  r11 = fmaf(oc * u.y, u.y, c);       r12 = fmaf(oc * u.y, u.z, -s * u.x);
-        r20 = fmaf(oc * u.z, u.x, -s * u.y); r21 = fmaf(oc * u.z, u.y, s * u.x); r22 = fmaf(oc * u.z, u.z, c);
-        t0 = b.x - (r00 * b.x + r01 * b.y + r02 * b.z);
-        t1 = b.y - (r10 * b.x + r11 * b.y + r12 * b.z);
-        t2 = b.z - (r20 * b.x + r21 * b.y + r22 * b.z);
-        const int4 fr = ldg(L.frag + r + 1);
-        parent = fr.z;
-        depth = fr.w;
-    }
-    // Forward kinematics, one tree level at a time: M_child = M_parent o L_k.
-    // Torsions are threads 0..T-1 < 32, all in warp 0.
+    // Warp 0: rigid-body transform and the torsion tree, one level at a time
+    // (M_child = M_parent o L_k; torsion k is lane k < 32).
     if (tm.warp() == 0) {
+        __syncwarp();
+        float qw = geno[3], qx = geno[4], qy = geno[5], qz = geno[6];
+        const float qn2 = qw * qw + qx * qx + qy * qy + qz * qz;
+        if (qn2 >= 1e-24f) {
+            const float qi = rsqrtf(qn2);
+            qw *= qi; qx *= qi; qy *= qi; qz *= qi;
+        } else {
+            qw = 1.f; qx = qy = qz = 0.f;
+        }
+        if (lane == 0) {
+            M[0] = make_float4(1.f - 2.f * (qy * qy + qz * qz), 2.f * (qx * qy - qw * qz), 2.f * (qx * qz + qw * qy), 0.f);
+            M[1] = make_float4(2.f * (qx * qy + qw * qz), 1.f - 2.f * (qx * qx + qz * qz), 2.f * (qy * qz - qw * qx), 0.f);
+            M[2] = make_float4(2.f * (qx * qz - qw * qy), 2.f * (qy * qz + qw * qx), 1.f - 2.f * (qx * qx + qy * qy), 0.f);
+        }
+        float r00 = 0, r01 = 0, r02 = 0, r10 = 0, r11 = 0, r12 = 0, r20 = 0, r21 = 0, r22 = 0, t0 = 0, t1 = 0, t2 = 0;
+        int depth = 0, parent = 0;
+        if (lane < T) {
+            float s, c;
+            sincosf(geno[ldg(L.tors_gene + lane)], &s, &c);
+            const float4 u = ldg(L.tors_u + lane), b = ldg(L.tors_b + lane);
+            const float oc = 1.f - c;
+            r00 = fmaf(oc * u.x, u.x, c);        r01 = fmaf(oc * u.x, u.y, -s * u.z); r02 = fmaf(oc * u.x, u.z, s * u.y);
+            r10 = fmaf(oc * u.y, u.x, s * u.z);  r11 = fmaf(oc * u.y, u.y, c);       r12 = fmaf(oc * u.y, u.z, -s * u.x);
+            r20 = fmaf(oc * u.z, u.x, -s * u.y); r21 = fmaf(oc * u.z, u.y, s * u.x); r22 = fmaf(oc * u.z, u.z, c);
+            t0 = b.x - (r00 * b.x + r01 * b.y + r02 * b.z);
+            t1 = b.y - (r10 * b.x + r11 * b.y + r12 * b.z);
+            t2 = b.z - (r20 * b.x + r21 * b.y + r22 * b.z);
+            const int4 fr = ldg(L.frag + lane + 1);
+            parent = fr.z;
+            depth = fr.w;
+        }
         for (int d = 1; d <= L.max_depth; ++d) {
             __syncwarp();
-            if (r < T && depth == d) {
+            if (lane < T && depth == d) {
                 const float4 p0 = M[3 * parent], p1 = M[3 * parent + 1], p2 = M[3 * parent + 2];
-                float4 *o = M + 3 * (r + 1);
+                float4 *o = M + 3 * (lane + 1);
                 o[0] = make_float4(p0.x * r00 + p0.y * r10 + p0.z * r20, p0.x * r01 + p0.y * r11 + p0.z * r21,
                                    p0.x * r02 + p0.y * r12 + p0.z * r22, p0.x * t0 + p0.y * t1 + p0.z * t2 + p0.w);
                 o[1] = make_float4(p1.x * r00 + p1.y * r10 + p1.z * r20, p1.x * r01 + p1.y * r11 + p1.z * r21,
@@ -277,21 +276,29 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
             }
         }
     }
+    // Per-group force partials start at zero.
+    if (GRAD)
+        for (int k = r; k < 4 * W * NB; k += S) PF[k] = make_float4(0.f, 0.f, 0.f, 0.f);
     tm.sync();
 
-    // Atom positions (relative to t).
-    for (int i = r; i < N; i += S) {
-        const float4 p = ldg(L.ref + i);
-        const int f = ldg(L.meta + i) >> 8;
-        const float4 m0 = M[3 * f], m1 = M[3 * f + 1], m2 = M[3 * f + 2];
-        X[i] = make_float4(fmaf(m0.x, p.x, fmaf(m0.y, p.y, fmaf(m0.z, p.z, m0.w))),
-                           fmaf(m1.x, p.x, fmaf(m1.y, p.y, fmaf(m1.z, p.z, m1.w))),
-                           fmaf(m2.x, p.x, fmaf(m2.y, p.y, fmaf(m2.z, p.z, m2.w))), 0.f);
+    // Atom positions relative to t (padding atoms up to a multiple of 8 at 0).
+    for (int i = r; i < NB; i += S) {
+        float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (i < N) {
+            const float4 p = ldg(L.ref + i);
+            const int f = ldg(L.meta + i) >> 8;
+            const float4 m0 = M[3 * f], m1 = M[3 * f + 1], m2 = M[3 * f + 2];
+            x = make_float4(fmaf(m0.x, p.x, fmaf(m0.y, p.y, fmaf(m0.z, p.z, m0.w))),
+                            fmaf(m1.x, p.x, fmaf(m1.y, p.y, fmaf(m1.z, p.z, m1.w))),
+                            fmaf(m2.x, p.x, fmaf(m2.y, p.y, fmaf(m2.z, p.z, m2.w))), 0.f);
+        }
+        X[i] = x;
     }
     tm.sync();
 
     // Particle-grid reads of the thread's first atom go out first; the pair
-    // loop runs while they are in flight.
+    // rounds run while they are in flight.
+    const float tx = geno[0], ty = geno[1], tz = geno[2];
     const float tux = (tx - G.ox) * G.inv_h, tuy = (ty - G.oy) * G.inv_h, tuz = (tz - G.oz) * G.inv_h;
     float4 *Fv = reinterpret_cast<float4 *>(ws + Y.f);
     AtomCells A0;
@@ -300,18 +307,64 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
         atom_fetch(G, ldg(G.map_of_type + (ldg(L.meta + r) & 255)), ldg(L.ref + r).w, fmaf(xi.x, G.inv_h, tux),
                    fmaf(xi.y, G.inv_h, tuy), fmaf(xi.z, G.inv_h, tuz), A0);
     }
-    // Intramolecular pairs, strided over the team; s_p = (dE/dr)/r kept per pair.
+
+    // Intramolecular pairs, systolic: lane l of group q holds its own atom of
+    // block A and, travelling one lane per round, the force owed to the atom
+    // of block B it meets; both return to per-group partials PF[q][atom].
     float e = 0.f;
-    float *Sp = ws + Y.s;
-#pragma unroll 2
-    for (int p = r; p < P; p += S) {
-        const uint32_t ij = ldg(L.pair_ij + p);
-        const float4 xi = X[ij & 0xffffu], xj = X[ij >> 16];
-        const float ddx = xi.x - xj.x, ddy = xi.y - xj.y, ddz = xi.z - xj.z;
-        const float r2 = fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz));
-        float s = 0.f;
-        if (r2 < kCut2) e += pair_energy<GRAD>(r2, ldg(L.pair_c + p), ldg(L.pair_ds + p), s);
-        if (GRAD) Sp[p] = s;
+    {
+        const SchedDev &SD = L.sched[W == 1 ? 0 : W == 2 ? 1 : W == 4 ? 2 : 3];
+        const int w = tm.warp(), q = 4 * w + (lane >> 3), sl = lane & 7, gb = lane & ~7;
+        const int base = SD.base[w], nr = SD.rounds[w];
+        float4 xa = make_float4(0.f, 0.f, 0.f, 0.f);
+        float ax = 0.f, ay = 0.f, az = 0.f, bx = 0.f, by = 0.f, bz = 0.f;
+        float4 *pq = PF + q * NB;
+        for (int rr = 0; rr < nr; ++rr) {
+            const int idx = base + rr;
+            const uint32_t ctl = ldg(SD.ctrl + 4 * idx + (lane >> 3));
+            const float4 c = ldg(SD.rec4 + 32 * idx + lane);
+            const float ds = ldg(SD.recd + 32 * idx + lane);
+            const int A = SCH_A(ctl), B = SCH_B(ctl), d = SCH_D(ctl);
+            if (ctl & SCH_FIRST) {
+                xa = X[8 * A + sl];
+                ax = ay = az = bx = by = bz = 0.f;
+            }
+            const float4 xb = X[8 * B + ((sl + d) & 7)];
+            const float ddx = xa.x - xb.x, ddy = xa.y - xb.y, ddz = xa.z - xb.z;
+            const float r2 = fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz));
+            float s = 0.f;
+            if (r2 < kCut2) e += pair_energy<GRAD>(r2, c, ds, s);
+            if (GRAD) {
+                const float fx = s * ddx, fy = s * ddy, fz = s * ddz;
+                ax += fx; ay += fy; az += fz;
+                bx -= fx; by -= fy; bz -= fz;
+                const int nxt = gb | ((sl + 1) & 7);
+                bx = __shfl_sync(0xffffffffu, bx, nxt);
+                by = __shfl_sync(0xffffffffu, by, nxt);
+                bz = __shfl_sync(0xffffffffu, bz, nxt);
+                const bool last = (ctl & SCH_LAST) != 0;
+                if (__any_sync(0xffffffffu, last)) {
+                    // the force owed to atom sl of block B sits d+1 lanes back
+                    const int src = gb | ((sl - d - 1) & 7);
+                    const float rx = __shfl_sync(0xffffffffu, bx, src);
+                    const float ry = __shfl_sync(0xffffffffu, by, src);
+                    const float rz = __shfl_sync(0xffffffffu, bz, src);
+                    if (last && (ctl & SCH_VALID)) {
+                        float4 pa = pq[8 * A + sl];
+                        if (ctl & SCH_DIAG) {
+                            pa.x += ax + rx; pa.y += ay + ry; pa.z += az + rz;
+                            pq[8 * A + sl] = pa;
+                        } else {
+                            pa.x += ax; pa.y += ay; pa.z += az;
+                            pq[8 * A + sl] = pa;
+                            float4 pb = pq[8 * B + sl];
+                            pb.x += rx; pb.y += ry; pb.z += rz;
+                            pq[8 * B + sl] = pb;
+                        }
+                    }
+                }
+            }
+        }
     }
     for (int i = r; i < N; i += S) {
         if (i != r) {
@@ -326,34 +379,27 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
     if (!GRAD) return team_sum(tm, e, red);
     tm.sync();
 
-    // Forces: dE/dx_i += s_p (x_i - x_partner) over the atom's pairs, each
-    // atom's CSR list split over k lanes, summed by a butterfly.  Per atom also
-    // (x_i - t) x f_i for the torque and torsion sums.
+    // Per-atom force = grid part + the 4W group partials (k lanes per atom,
+    // partials in group order, butterfly); torque (x_i - t) x f_i.
     float4 *Tq = reinterpret_cast<float4 *>(ws + Y.tq);
     {
-        const int k = lanes_per_item(N, S), per = S / k, sub = r & (k - 1);
-        for (int base = 0; base < N; base += per) {
-            const int i = base + r / k;
+        constexpr int NG = 4 * W;
+        const int k = lanes_per_item(N, S) < NG ? lanes_per_item(N, S) : NG;
+        const int per = S / k, sub = r & (k - 1);
+        for (int b0 = 0; b0 < N; b0 += per) {
+            const int i = b0 + r / k;
             const bool act = i < N;
             float fx = 0.f, fy = 0.f, fz = 0.f;
-            float4 xi = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (act) {
-                xi = X[i];
-                const int e1 = ldg(L.adj_off + i + 1);
-                for (int q = ldg(L.adj_off + i) + sub; q < e1; q += k) {
-                    const uint32_t a = ldg(L.adj + q);
-                    const float s = Sp[a & 0xffffu];
-                    const float4 xo = X[a >> 16];
-                    fx = fmaf(s, xi.x - xo.x, fx);
-                    fy = fmaf(s, xi.y - xo.y, fy);
-                    fz = fmaf(s, xi.z - xo.z, fz);
+            if (act)
+                for (int g = sub; g < NG; g += k) {
+                    const float4 v = PF[g * NB + i];
+                    fx += v.x; fy += v.y; fz += v.z;
                 }
-            }
             fx = group_sum(fx, k);
             fy = group_sum(fy, k);
             fz = group_sum(fz, k);
             if (act && sub == 0) {
-                const float4 g = Fv[i];
+                const float4 g = Fv[i], xi = X[i];
                 fx += g.x; fy += g.y; fz += g.z;
                 Fv[i] = make_float4(fx, fy, fz, 0.f);
                 Tq[i] = make_float4(xi.y * fz - xi.z * fy, xi.z * fx - xi.x * fz, xi.x * fy - xi.y * fx, 0.f);
@@ -362,13 +408,16 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
     }
     tm.sync();
 
-    // Per-fragment sums of f_i and (x_i - t) x f_i (m lanes per fragment).
+    // Gradient.  W = 1: per-fragment sums first, then torsion k sums the
+    // fragments it moves (a contiguous run in depth-first order).  W > 1:
+    // torsion k sums its contiguous atom range directly.  Range T is the
+    // whole ligand (translation and rotation).  m lanes per range, butterfly.
     float4 *FS = reinterpret_cast<float4 *>(ws + Y.fs);
     const int F = L.n_frag;
-    {
+    if (W == 1) {
         const int m = lanes_per_item(F, S), per = S / m, sub = r & (m - 1);
-        for (int base = 0; base < F; base += per) {
-            const int f = base + r / m;
+        for (int b0 = 0; b0 < F; b0 += per) {
+            const int f = b0 + r / m;
             const bool act = f < F;
             int lo = 0, hi = 0;
             if (act) {
@@ -378,9 +427,9 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
             }
             float a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0, a5 = 0;
             for (int i = lo + sub; i < hi; i += m) {
-                const float4 fv = Fv[i], tq = Tq[i];
+                const float4 fv = Fv[i], t = Tq[i];
                 a0 += fv.x; a1 += fv.y; a2 += fv.z;
-                a3 += tq.x; a4 += tq.y; a5 += tq.z;
+                a3 += t.x; a4 += t.y; a5 += t.z;
             }
             a0 = group_sum(a0, m); a1 = group_sum(a1, m); a2 = group_sum(a2, m);
             a3 = group_sum(a3, m); a4 = group_sum(a4, m); a5 = group_sum(a5, m);
@@ -389,26 +438,30 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
                 FS[2 * f + 1] = make_float4(a3, a4, a5, 0.f);
             }
         }
+        tm.sync();
     }
-    tm.sync();
-
-    // Gradient: range k < T is the fragments torsion k moves (a contiguous
-    // run in depth-first order), range T is all fragments (translation and
-    // rotation); m lanes per range and a butterfly.
     float *grad = ws + Y.grad;
     {
         const int R = T + 1, m = lanes_per_item(R, S), per = S / m, sub = r & (m - 1);
-        for (int base = 0; base < R; base += per) {
-            const int k = base + r / m;
+        for (int b0 = 0; b0 < R; b0 += per) {
+            const int k = b0 + r / m;
             const bool act = k < R;
             int lo = 0, hi = 0;
             if (act) {
-                lo = k < T ? k + 1 : 0;
-                hi = k < T ? ldg(L.sub_end + k + 1) : F;
+                if (W == 1) {
+                    lo = k < T ? k + 1 : 0;
+                    hi = k < T ? ldg(L.sub_end + k + 1) : F;
+                } else if (k < T) {
+                    const int2 rg = ldg(L.tors_range + k);
+                    lo = rg.x;
+                    hi = rg.y;
+                } else {
+                    hi = N;
+                }
             }
             float a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0, a5 = 0;
-            for (int f = lo + sub; f < hi; f += m) {
-                const float4 u = FS[2 * f], v = FS[2 * f + 1];
+            for (int j = lo + sub; j < hi; j += m) {
+                const float4 u = W == 1 ? FS[2 * j] : Fv[j], v = W == 1 ? FS[2 * j + 1] : Tq[j];
                 a0 += u.x; a1 += u.y; a2 += u.z;
                 a3 += v.x; a4 += v.y; a5 += v.z;
             }
@@ -426,6 +479,15 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
                     const float cz = a5 - (xb.x * a1 - xb.y * a0);
                     grad[ldg(L.tors_gene + k)] = fmaf(ux, cx, fmaf(uy, cy, uz * cz));
                 } else {  // dE/dt = sum f; dE/dq = 2 ((0, G) (x) qhat) / |q|, G = torque about t
+                    float qw = geno[3], qx = geno[4], qy = geno[5], qz = geno[6];
+                    const float qn2 = qw * qw + qx * qx + qy * qy + qz * qz;
+                    float qinv = 0.f;
+                    if (qn2 >= 1e-24f) {
+                        qinv = rsqrtf(qn2);
+                        qw *= qinv; qx *= qinv; qy *= qinv; qz *= qinv;
+                    } else {
+                        qw = 1.f; qx = qy = qz = 0.f;
+                    }
                     grad[0] = a0; grad[1] = a1; grad[2] = a2;
                     const float k2 = 2.f * qinv;
                     grad[3] = k2 * (-a3 * qx - a4 * qy - a5 * qz);

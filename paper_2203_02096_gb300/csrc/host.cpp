@@ -355,6 +355,87 @@ struct Blob {
     }
 };
 
+// Systolic pair schedule for a team of W warps (see SchedDev): block pairs
+// holding at least one listed pair, assigned longest-first to the least
+// loaded of the 4W groups (lowest group on ties); each warp runs as many
+// rounds as its busiest group.  Pairs outside the list get zero records.
+struct SchedHost {
+    std::vector<uint32_t> ctrl;
+    std::vector<float4> rec4;
+    std::vector<float> recd;
+    int base[8] = {0}, rounds[8] = {0};
+    long long listed = 0;  // non-zero pair slots (must equal the pair count)
+};
+
+SchedHost build_sched(int n, int W, const std::vector<int> &pidx, const std::vector<float4> &pc,
+                      const std::vector<float> &pds) {
+    const int nb = (n + 7) / 8, NG = 4 * W;
+    struct BP {
+        int A, B, rounds;
+    };
+    std::vector<BP> bps;
+    for (int A = 0; A < nb; ++A)
+        for (int B = A; B < nb; ++B) {
+            bool any = false;
+            for (int a = 8 * A; a < 8 * A + 8 && a < n && !any; ++a)
+                for (int b = (A == B ? a + 1 : 8 * B); b < 8 * B + 8 && b < n && !any; ++b)
+                    any = pidx[(size_t)a * n + b] >= 0;
+            if (any) bps.push_back({A, B, A == B ? 4 : 8});
+        }
+    std::vector<int> order(bps.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return bps[x].rounds > bps[y].rounds; });
+    std::vector<std::vector<int>> glist(NG);
+    std::vector<int> load(NG, 0);
+    for (int idx : order) {
+        int g = 0;
+        for (int k = 1; k < NG; ++k)
+            if (load[k] < load[g]) g = k;
+        glist[g].push_back(idx);
+        load[g] += bps[idx].rounds;
+    }
+    SchedHost S;
+    int off = 0;
+    for (int w = 0; w < 8; ++w) {
+        int R = 0;
+        if (w < W)
+            for (int q = 0; q < 4; ++q) R = std::max(R, load[4 * w + q]);
+        S.base[w] = off;
+        S.rounds[w] = R;
+        off += R;
+    }
+    S.ctrl.assign((size_t)std::max(off, 1) * 4, 0u);
+    S.rec4.assign((size_t)std::max(off, 1) * 32, make_float4(0.f, 0.f, 0.f, 0.f));
+    S.recd.assign((size_t)std::max(off, 1) * 32, 0.f);
+    for (int w = 0; w < W; ++w)
+        for (int q = 0; q < 4; ++q) {
+            int round = S.base[w];
+            for (int bi : glist[4 * w + q]) {
+                const BP &bp = bps[bi];
+                const bool diag = bp.A == bp.B;
+                for (int t = 0; t < bp.rounds; ++t, ++round) {
+                    const int d = diag ? t + 1 : t;
+                    uint32_t c = (uint32_t)bp.A | ((uint32_t)bp.B << 5) | ((uint32_t)d << 10) | SCH_VALID;
+                    if (t == 0) c |= SCH_FIRST;
+                    if (t == bp.rounds - 1) c |= SCH_LAST;
+                    if (diag) c |= SCH_DIAG;
+                    S.ctrl[4 * (size_t)round + q] = c;
+                    for (int sl = 0; sl < 8; ++sl) {
+                        const int a = 8 * bp.A + sl, b = 8 * bp.B + ((sl + d) & 7);
+                        if (a >= n || b >= n || (diag && d == 4 && sl >= 4)) continue;
+                        const int i = std::min(a, b), j = std::max(a, b);
+                        const int pp = pidx[(size_t)i * n + j];
+                        if (pp < 0) continue;
+                        S.rec4[32 * (size_t)round + 8 * q + sl] = pc[pp];
+                        S.recd[32 * (size_t)round + 8 * q + sl] = pds[pp];
+                        ++S.listed;
+                    }
+                }
+            }
+        }
+    return S;
+}
+
 }  // namespace
 
 extern "C" int load_ligand(dock_ctx *ctx, int n, const double *xyz, const int *type, const double *charge, int nb,
@@ -537,6 +618,13 @@ extern "C" int load_ligand(dock_ctx *ctx, int n, const double *xyz, const int *t
             pc64.insert(pc64.end(), {c12, c6, c10, qq, ds});
         }
     const int P = (int)pij.size();
+    std::vector<int> pidx((size_t)n * n, -1);
+    for (int p = 0; p < P; ++p) pidx[(size_t)(pij[p] & 0xffff) * n + (pij[p] >> 16)] = p;
+    SchedHost sched[4];
+    for (int k = 0; k < 4; ++k) {
+        sched[k] = build_sched(n, 1 << k, pidx, pc, pds);
+        if (sched[k].listed != P) return set_err(ctx, DOCK_ERR_INVALID, "internal error: pair schedule incomplete");
+    }
     std::vector<std::vector<uint32_t>> lists(n);
     for (int p = 0; p < P; ++p) {
         const int i = pij[p] & 0xffff, j = pij[p] >> 16;
@@ -572,6 +660,12 @@ extern "C" int load_ligand(dock_ctx *ctx, int n, const double *xyz, const int *t
     const size_t o_r64 = B.add(ref64.data(), 3 * n * sizeof(double));
     const size_t o_pc64 = B.add(pc64.data(), pc64.size() * sizeof(double));
     const size_t o_q64 = B.add(q64.data(), n * sizeof(double));
+    size_t o_sc[4], o_sr4[4], o_srd[4];
+    for (int k = 0; k < 4; ++k) {
+        o_sc[k] = B.add(sched[k].ctrl.data(), sched[k].ctrl.size() * sizeof(uint32_t));
+        o_sr4[k] = B.add(sched[k].rec4.data(), sched[k].rec4.size() * sizeof(float4));
+        o_srd[k] = B.add(sched[k].recd.data(), sched[k].recd.size() * sizeof(float));
+    }
 
     dock_ligand *L = new dock_ligand();
     L->blob_bytes = B.bytes.size();
@@ -613,6 +707,16 @@ extern "C" int load_ligand(dock_ctx *ctx, int n, const double *xyz, const int *t
     d.ref64 = (const double *)(base + o_r64);
     d.pair_c64 = (const double *)(base + o_pc64);
     d.q64 = (const double *)(base + o_q64);
+    d.nb8 = (n + 7) & ~7;
+    for (int k = 0; k < 4; ++k) {
+        d.sched[k].ctrl = (const uint32_t *)(base + o_sc[k]);
+        d.sched[k].rec4 = (const float4 *)(base + o_sr4[k]);
+        d.sched[k].recd = (const float *)(base + o_srd[k]);
+        for (int w = 0; w < 8; ++w) {
+            d.sched[k].base[w] = sched[k].base[w];
+            d.sched[k].rounds[w] = sched[k].rounds[w];
+        }
+    }
     L->types = types;
     *out = L;
     return DOCK_OK;
@@ -648,7 +752,7 @@ static int score_common(dock_ctx *ctx, const dock_grids *g, const dock_ligand *l
     int rc = check_maps(ctx, g, l);
     if (rc) return rc;
     if (B == 0) return DOCK_OK;
-    const EvalLayout W = eval_layout(l->dev.n_atoms, l->dev.n_frag, l->dev.n_pairs, grad != nullptr);
+    const EvalLayout W = eval_layout(l->dev.n_atoms, l->dev.n_frag, l->dev.nb8, grad != nullptr, 1);
     if (!evaluator_smem_ok(ctx, W, 1)) return set_err(ctx, DOCK_ERR_SIZE, "ligand too large for shared memory");
     cudaError_t e = launch_score(ctx, l->dev, g->dev, geno, B, E, grad, (cudaStream_t)stream);
     return e ? cuda_err(ctx, e, "score kernel") : DOCK_OK;
@@ -669,7 +773,7 @@ int pose_batch(dock_ctx *ctx, const dock_ligand *l, const float *geno, int B, fl
     if (!ctx) return DOCK_ERR_INVALID;
     if (!l || B < 0 || (B > 0 && (!geno || !xyz))) return set_err(ctx, DOCK_ERR_INVALID, "invalid argument");
     if (B == 0) return DOCK_OK;
-    const EvalLayout W = eval_layout(l->dev.n_atoms, l->dev.n_frag, l->dev.n_pairs, false);
+    const EvalLayout W = eval_layout(l->dev.n_atoms, l->dev.n_frag, l->dev.nb8, false, 1);
     if (!evaluator_smem_ok(ctx, W, 1)) return set_err(ctx, DOCK_ERR_SIZE, "ligand too large for shared memory");
     cudaError_t e = launch_pose(ctx, l->dev, geno, B, xyz, (cudaStream_t)stream);
     return e ? cuda_err(ctx, e, "pose kernel") : DOCK_OK;

@@ -16,8 +16,33 @@
 // torsion tree (fragment 0 = root); then the atoms moved by the torsion
 // entering fragment f are exactly the fragments [f, sub_end[f]).  Internal
 // torsion k is the bond entering fragment k+1.
+// Systolic pair schedule for a team of W warps (4W groups of 8 lanes).
+// Atoms form blocks of 8; a group processes a list of block pairs (A, B),
+// 8 rounds each (4 when A == B); in round d lane l pairs atom 8A + l with
+// atom 8B + (l + d) mod 8.  ctrl[round][group of the warp] packs A, B, d and
+// flags; rec4/recd[round][lane] hold the pair coefficients (c12, c6, c10,
+// qq) and the desolvation factor, zero for pairs outside the pair list.
+struct SchedDev {
+    const uint32_t *ctrl;
+    const float4 *rec4;
+    const float *recd;
+    int base[8];    // first round of warp w
+    int rounds[8];  // rounds of warp w
+};
+
+// ctrl bit fields
+#define SCH_A(c) ((c) & 31u)
+#define SCH_B(c) (((c) >> 5) & 31u)
+#define SCH_D(c) (((c) >> 10) & 7u)
+#define SCH_FIRST 0x2000u
+#define SCH_LAST 0x4000u
+#define SCH_DIAG 0x8000u
+#define SCH_VALID 0x10000u
+
 struct LigandDev {
     int n_atoms, n_tors, n_frag, n_pairs, n_genes, max_depth;
+    int nb8;                  // atoms rounded up to a multiple of 8
+    SchedDev sched[4];        // for W = 1, 2, 4, 8
     const float4 *ref;        // [n] centred reference coords, w = partial charge
     const int *meta;          // [n] type | fragment << 8
     const int *perm;          // [n] internal atom -> input atom
@@ -56,12 +81,13 @@ struct GridDev {
 // Shared-memory scratch of one evaluating team, offsets in floats (each a
 // multiple of 4 so float4 views are aligned).
 struct EvalLayout {
-    int geno, grad, red, M, fs, x, f, tq, s, total;
+    int geno, grad, red, M, fs, x, f, tq, pf, total;
 };
 
 __host__ __device__ inline int round4(int v) { return (v + 3) & ~3; }
 
-__host__ __device__ inline EvalLayout eval_layout(int n_atoms, int n_frag, int n_pairs, bool grad) {
+// W: warps of the team (partials: 4W groups x nb8 atoms).
+__host__ __device__ inline EvalLayout eval_layout(int n_atoms, int n_frag, int nb8, bool grad, int W) {
     EvalLayout w;
     int o = 0;
     w.geno = o; o += 48;
@@ -69,10 +95,10 @@ __host__ __device__ inline EvalLayout eval_layout(int n_atoms, int n_frag, int n
     w.red = o; o += 32;
     w.M = o; o += 12 * n_frag;
     w.fs = o; o += grad ? 8 * n_frag : 0;
-    w.x = o; o += 4 * n_atoms;
+    w.x = o; o += 4 * nb8;
     w.f = o; o += grad ? 4 * n_atoms : 0;
     w.tq = o; o += grad ? 4 * n_atoms : 0;
-    w.s = o; o += grad ? round4(n_pairs) : 0;
+    w.pf = o; o += grad ? 4 * 4 * W * nb8 : 0;
     w.total = round4(o);
     return w;
 }

@@ -130,7 +130,7 @@ int pick_warps(dock_ctx *ctx, const EvalLayout &W) {
 cudaError_t launch_score(dock_ctx *ctx, const LigandDev &L, const GridDev &G, const float *geno, int B, float *E,
                          float *grad, cudaStream_t s) {
     const bool g = grad != nullptr;
-    EvalLayout W = eval_layout(L.n_atoms, L.n_frag, L.n_pairs, g);
+    EvalLayout W = eval_layout(L.n_atoms, L.n_frag, L.nb8, g, 1);
     const int wpb = pick_warps(ctx, W);
     const size_t smem = (size_t)W.total * sizeof(float) * wpb;
     LigandDev l = L;
@@ -143,7 +143,7 @@ cudaError_t launch_score(dock_ctx *ctx, const LigandDev &L, const GridDev &G, co
 }
 
 cudaError_t launch_pose(dock_ctx *ctx, const LigandDev &L, const float *geno, int B, float *xyz, cudaStream_t s) {
-    EvalLayout W = eval_layout(L.n_atoms, L.n_frag, L.n_pairs, false);
+    EvalLayout W = eval_layout(L.n_atoms, L.n_frag, L.nb8, false, 1);
     const int wpb = pick_warps(ctx, W);
     const size_t smem = (size_t)W.total * sizeof(float) * wpb;
     LigandDev l = L;

@@ -310,7 +310,7 @@ ls_kernel(LigandDev L, GridDev G, float *x_in, float *E_pop, const int *__restri
     const dev::Team<W> tm(W == 1 ? (threadIdx.x & 31) : threadIdx.x);
     const int c = W == 1 ? blockIdx.x * (blockDim.x >> 5) + team_in_block : blockIdx.x;
     if (c >= nchains) return;  // uniform over the team
-    const int Gn = L.n_genes, S = dev::Team<W>::kSize;
+    const int Gn = L.n_genes;
     float *xi, *xo, *eo;
     int run = 0;
     if (picks) {
@@ -324,44 +324,52 @@ ls_kernel(LigandDev L, GridDev G, float *x_in, float *E_pop, const int *__restri
         xo = x_out + (size_t)c * Gn;
         eo = E_out + c;
     }
-    // thread r owns genes r and r + S (the second only when S = 32)
-    const int j0 = tm.rank, j1 = tm.rank + S;
-    float x0 = j0 < Gn ? xi[j0] : 0.f, x1 = j1 < Gn ? xi[j1] : 0.f;
+    // warp 0 owns the genes: lane l holds genes l and l + 32
+    const bool w0 = tm.warp() == 0;
+    const int lane = threadIdx.x & 31, j0 = lane, j1 = lane + 32;
+    float x0 = 0.f, x1 = 0.f;
+    if (w0) {
+        x0 = j0 < Gn ? xi[j0] : 0.f;
+        x1 = j1 < Gn ? xi[j1] : 0.f;
+    }
     float b0 = x0, b1 = x1, best = INFINITY;
     float g2a = 0.f, g2b = 0.f, d2a = 0.f, d2b = 0.f;
     for (int it = 0; it < iters; ++it) {
-        if (j0 < Gn) ws[Y.geno + j0] = x0;
-        if (j1 < Gn) ws[Y.geno + j1] = x1;
-        tm.sync();
+        if (w0) {
+            if (j0 < Gn) ws[Y.geno + j0] = x0;
+            if (j1 < Gn) ws[Y.geno + j1] = x1;
+        }
+        // the evaluator's warp 0 reads the genes after a __syncwarp; the
+        // other warps read them only after the team's barriers
         const float e = dev::eval_team<W, true>(L, G, ws, Y, tm);
-        if (e < best) {
-            best = e;
-            b0 = x0;
-            b1 = x1;
+        if (w0) {
+            if (e < best) {
+                best = e;
+                b0 = x0;
+                b1 = x1;
+            }
+            if (j0 < Gn) {
+                adadelta(x0, ws[Y.grad + j0], g2a, d2a, rho, eps);
+                if (j0 >= 7) x0 = wrap_any(x0);
+            }
+            if (j1 < Gn) {
+                adadelta(x1, ws[Y.grad + j1], g2b, d2b, rho, eps);
+                x1 = wrap_any(x1);
+            }
         }
-        if (j0 < Gn) {
-            adadelta(x0, ws[Y.grad + j0], g2a, d2a, rho, eps);
-            if (j0 >= 7) x0 = wrap_any(x0);
-        }
-        if (j1 < Gn) {
-            adadelta(x1, ws[Y.grad + j1], g2b, d2b, rho, eps);
-            x1 = wrap_any(x1);
-        }
-        // no barrier needed here: the next writes (genes) touch a region no
-        // thread reads after the evaluator's last barrier
     }
     // best point, quaternion normalised (FP32, fixed order)
-    if (j0 < Gn) ws[Y.geno + j0] = b0;
-    if (j1 < Gn) ws[Y.geno + j1] = b1;
-    tm.sync();
-    const float q3 = ws[Y.geno + 3], q4 = ws[Y.geno + 4], q5 = ws[Y.geno + 5], q6 = ws[Y.geno + 6];
-    const float n = sqrtf(((q3 * q3 + q4 * q4) + q5 * q5) + q6 * q6);
-    if (j0 >= 3 && j0 < 7 && n > 0.f) b0 = b0 / n;
-    if (j0 < Gn) xo[j0] = b0;
-    if (j1 < Gn) xo[j1] = b1;
-    if (tm.rank == 0) {
-        *eo = best;
-        if (evals) atomicAdd(evals + run, (unsigned long long)iters);
+    if (w0) {
+        const float q3 = __shfl_sync(0xffffffffu, b0, 3), q4 = __shfl_sync(0xffffffffu, b0, 4);
+        const float q5 = __shfl_sync(0xffffffffu, b0, 5), q6 = __shfl_sync(0xffffffffu, b0, 6);
+        const float n = sqrtf(((q3 * q3 + q4 * q4) + q5 * q5) + q6 * q6);
+        if (j0 >= 3 && j0 < 7 && n > 0.f) b0 = b0 / n;
+        if (j0 < Gn) xo[j0] = b0;
+        if (j1 < Gn) xo[j1] = b1;
+        if (lane == 0) {
+            *eo = best;
+            if (evals) atomicAdd(evals + run, (unsigned long long)iters);
+        }
     }
 }
 
@@ -447,8 +455,9 @@ int resolve_params(dock_ctx *ctx, const dock_params *in, dock_params &p) {
 }
 
 // Warps per local-search chain: threads_req (32..256) when given, else
-// enough to put about 16 warps on every SM while chains are few.
-int ls_team_warps(const dock_ctx *ctx, int chains, int threads_req) {
+// enough to put about 16 warps on every SM while chains are few; never more
+// than fit in shared memory.
+int ls_team_warps(const dock_ctx *ctx, int chains, int threads_req, const LigandDev &L) {
     int w = 1;
     if (threads_req > 0) {
         w = threads_req / 32;
@@ -456,7 +465,9 @@ int ls_team_warps(const dock_ctx *ctx, int chains, int threads_req) {
         const long long target = 16LL * ctx->num_sms;
         while (w < 8 && (long long)chains * 2 * w <= target) w <<= 1;
     }
-    return w >= 8 ? 8 : w >= 4 ? 4 : w >= 2 ? 2 : 1;
+    w = w >= 8 ? 8 : w >= 4 ? 4 : w >= 2 ? 2 : 1;
+    while (w > 1 && (size_t)eval_layout(L.n_atoms, L.n_frag, L.nb8, true, w).total * 4 > ctx->smem_optin) w >>= 1;
+    return w;
 }
 
 // Launches ls_kernel<W>.  W = 1: four one-warp teams per block once the
@@ -502,8 +513,9 @@ int dock_async(dock_ctx *ctx, const dock_grids *grids, const dock_ligand *lig, c
     const LigandDev &L = lig->dev;
     const GridDev &G = grids->dev;
     const int Gn = L.n_genes, pop = P.pop_size, R = P.nruns, nls = P.ls_count;
-    const EvalLayout Wn = eval_layout(L.n_atoms, L.n_frag, L.n_pairs, false);
-    const EvalLayout Wg = eval_layout(L.n_atoms, L.n_frag, L.n_pairs, true);
+    const EvalLayout Wn = eval_layout(L.n_atoms, L.n_frag, L.nb8, false, 1);
+    const int lw = ls_team_warps(ctx, P.nruns * P.ls_count, P.ls_threads, L);
+    const EvalLayout Wg = eval_layout(L.n_atoms, L.n_frag, L.nb8, true, lw);
     if (!evaluator_smem_ok(ctx, Wg, 1)) return set_err(ctx, DOCK_ERR_SIZE, "ligand too large for shared memory");
     const int gw = evaluator_smem_ok(ctx, Wn, 4) ? 4 : 1;
     const size_t items = (size_t)R * pop;
@@ -530,7 +542,7 @@ int dock_async(dock_ctx *ctx, const dock_grids *grids, const dock_ligand *lig, c
         const long long per_gen = (long long)(pop - 1) + (long long)nls * P.ls_iters;
         long long ngen = 0;
         if (P.max_evals > pop) ngen = (P.max_evals - pop + per_gen - 1) / per_gen;
-        const int chains = R * nls, lw = ls_team_warps(ctx, chains, P.ls_threads);
+        const int chains = R * nls;
         long long *no_info = nullptr;
         float *no_out = nullptr;
         for (long long gen = 1; gen <= ngen && !e; ++gen) {
@@ -618,7 +630,7 @@ int dock_init_population(dock_ctx *ctx, const dock_grids *grids, int n_torsions,
     GaConst C = ga_const(P, n_torsions, nruns, seed);
     LigandDev l{};
     GridDev g = grids->dev;
-    EvalLayout w = eval_layout(1, 1, 0, false);
+    EvalLayout w = eval_layout(1, 1, 8, false, 1);
     float *no_e = nullptr;
     unsigned long long *no_ev = nullptr;
     void *a[] = {&l, &g, &C, &pop_out, &no_e, &no_ev, &w};
@@ -640,7 +652,7 @@ int dock_ga_children(dock_ctx *ctx, int n_torsions, int pop, int nruns, const fl
     GaConst C = ga_const(P, n_torsions, nruns, seed);
     LigandDev l{};
     GridDev g{};
-    EvalLayout w = eval_layout(1, 1, 0, false);
+    EvalLayout w = eval_layout(1, 1, 8, false, 1);
     float *no_e = nullptr;
     unsigned long long *no_ev = nullptr;
     long long *inf = (long long *)info;
@@ -671,11 +683,11 @@ int dock_local_search(dock_ctx *ctx, const dock_grids *grids, const dock_ligand 
     if (rc) return rc;
     if (B == 0) return DOCK_OK;
     const LigandDev &L = lig->dev;
-    EvalLayout W = eval_layout(L.n_atoms, L.n_frag, L.n_pairs, true);
-    if (!evaluator_smem_ok(ctx, W, 1)) return set_err(ctx, DOCK_ERR_SIZE, "ligand too large for shared memory");
     if (threads != 0 && threads != 32 && threads != 64 && threads != 128 && threads != 256)
         return set_err(ctx, DOCK_ERR_INVALID, "threads must be 0, 32, 64, 128 or 256");
-    const int lw = ls_team_warps(ctx, B, threads);
+    const int lw = ls_team_warps(ctx, B, threads, L);
+    EvalLayout W = eval_layout(L.n_atoms, L.n_frag, L.nb8, true, lw);
+    if (!evaluator_smem_ok(ctx, W, 1)) return set_err(ctx, DOCK_ERR_SIZE, "ligand too large for shared memory");
     LigandDev l = L;
     GridDev g = grids->dev;
     float *xin = const_cast<float *>(x0);
@@ -750,8 +762,9 @@ extern "C" int dock_async_noalloc(dock_ctx *ctx, const dock_grids *grids, const 
     const LigandDev &L = lig->dev;
     const GridDev &G = grids->dev;
     const int Gn = L.n_genes, pop = P.pop_size, R = P.nruns, nls = P.ls_count;
-    const EvalLayout Wn = eval_layout(L.n_atoms, L.n_frag, L.n_pairs, false);
-    const EvalLayout Wg = eval_layout(L.n_atoms, L.n_frag, L.n_pairs, true);
+    const EvalLayout Wn = eval_layout(L.n_atoms, L.n_frag, L.nb8, false, 1);
+    const int lw = ls_team_warps(ctx, P.nruns * P.ls_count, P.ls_threads, L);
+    const EvalLayout Wg = eval_layout(L.n_atoms, L.n_frag, L.nb8, true, lw);
     if (!evaluator_smem_ok(ctx, Wg, 1)) return set_err(ctx, DOCK_ERR_SIZE, "ligand too large for shared memory");
     const int gw = evaluator_smem_ok(ctx, Wn, 4) ? 4 : 1;
     const size_t items = (size_t)R * pop;
@@ -786,7 +799,7 @@ extern "C" int dock_async_noalloc(dock_ctx *ctx, const dock_grids *grids, const 
     const long long per_gen = (long long)(pop - 1) + (long long)nls * P.ls_iters;
     long long ngen = 0;
     if (P.max_evals > pop) ngen = (P.max_evals - pop + per_gen - 1) / per_gen;
-    const int chains = R * nls, lw = ls_team_warps(ctx, chains, P.ls_threads);
+    const int chains = R * nls;
     long long *no_info = nullptr;
     float *no_out = nullptr;
     for (long long gen = 1; gen <= ngen && !e; ++gen) {
