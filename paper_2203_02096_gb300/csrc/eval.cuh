@@ -162,15 +162,11 @@ __device__ __forceinline__ float pair_energy(float r2, float4 c, float ds, float
     const float eel = c.w * __fdividef(rinv, eps);
     const float eds = ds * __expf(-r2e * kHalfInvSig2);
     if (GRAD) {
-        if (r2 >= kFloor2) {
-            const float dv = (-12.f * c.x * ri12 + 6.f * c.y * ri6 + 10.f * c.z * ri10) * rinv;
-            const float deps = __fdividef(kDielDeps * ex, den * den);
-            const float del = -eel * __fdividef(fmaf(r, deps, eps), eps * r);
-            const float dds = -eds * r * kInvSig2;
-            s = (dv + del + dds) * rinv;
-        } else {
-            s = 0.f;
-        }
+        const float dv = (-12.f * c.x * ri12 + 6.f * c.y * ri6 + 10.f * c.z * ri10) * rinv;
+        const float deps = __fdividef(kDielDeps * ex, den * den);
+        const float del = -eel * __fdividef(fmaf(r, deps, eps), eps * r);
+        const float dds = -eds * r * kInvSig2;
+        s = r2 >= kFloor2 ? (dv + del + dds) * rinv : 0.f;
     }
     return ev + eel + eds;
 }
@@ -308,61 +304,48 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
                    fmaf(xi.y, G.inv_h, tuy), fmaf(xi.z, G.inv_h, tuz), A0);
     }
 
-    // Intramolecular pairs, systolic: lane l of group q holds its own atom of
-    // block A and, travelling one lane per round, the force owed to the atom
-    // of block B it meets; both return to per-group partials PF[q][atom].
+    // Intramolecular pairs, systolic: in a step, lane l of group q holds its
+    // own atom of block A and, passed one lane along per round, the force
+    // owed to the atom of block B it meets; after 8 rounds that force is back
+    // at the lane owning the B atom, and both go to the group's partials.
     float e = 0.f;
     {
         const SchedDev &SD = L.sched[W == 1 ? 0 : W == 2 ? 1 : W == 4 ? 2 : 3];
         const int w = tm.warp(), q = 4 * w + (lane >> 3), sl = lane & 7, gb = lane & ~7;
-        const int base = SD.base[w], nr = SD.rounds[w];
-        float4 xa = make_float4(0.f, 0.f, 0.f, 0.f);
-        float ax = 0.f, ay = 0.f, az = 0.f, bx = 0.f, by = 0.f, bz = 0.f;
+        const int nxt = gb | ((sl + 1) & 7);
         float4 *pq = PF + q * NB;
-        for (int rr = 0; rr < nr; ++rr) {
-            const int idx = base + rr;
-            const uint32_t ctl = ldg(SD.ctrl + 4 * idx + (lane >> 3));
-            const float4 c = ldg(SD.rec4 + 32 * idx + lane);
-            const float ds = ldg(SD.recd + 32 * idx + lane);
-            const int A = SCH_A(ctl), B = SCH_B(ctl), d = SCH_D(ctl);
-            if (ctl & SCH_FIRST) {
-                xa = X[8 * A + sl];
-                ax = ay = az = bx = by = bz = 0.f;
-            }
-            const float4 xb = X[8 * B + ((sl + d) & 7)];
-            const float ddx = xa.x - xb.x, ddy = xa.y - xb.y, ddz = xa.z - xb.z;
-            const float r2 = fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz));
-            float s = 0.f;
-            if (r2 < kCut2) e += pair_energy<GRAD>(r2, c, ds, s);
-            if (GRAD) {
-                const float fx = s * ddx, fy = s * ddy, fz = s * ddz;
-                ax += fx; ay += fy; az += fz;
-                bx -= fx; by -= fy; bz -= fz;
-                const int nxt = gb | ((sl + 1) & 7);
-                bx = __shfl_sync(0xffffffffu, bx, nxt);
-                by = __shfl_sync(0xffffffffu, by, nxt);
-                bz = __shfl_sync(0xffffffffu, bz, nxt);
-                const bool last = (ctl & SCH_LAST) != 0;
-                if (__any_sync(0xffffffffu, last)) {
-                    // the force owed to atom sl of block B sits d+1 lanes back
-                    const int src = gb | ((sl - d - 1) & 7);
-                    const float rx = __shfl_sync(0xffffffffu, bx, src);
-                    const float ry = __shfl_sync(0xffffffffu, by, src);
-                    const float rz = __shfl_sync(0xffffffffu, bz, src);
-                    if (last && (ctl & SCH_VALID)) {
-                        float4 pa = pq[8 * A + sl];
-                        if (ctl & SCH_DIAG) {
-                            pa.x += ax + rx; pa.y += ay + ry; pa.z += az + rz;
-                            pq[8 * A + sl] = pa;
-                        } else {
-                            pa.x += ax; pa.y += ay; pa.z += az;
-                            pq[8 * A + sl] = pa;
-                            float4 pb = pq[8 * B + sl];
-                            pb.x += rx; pb.y += ry; pb.z += rz;
-                            pq[8 * B + sl] = pb;
-                        }
-                    }
+        const int s0 = SD.base[w], s1 = s0 + SD.steps[w];
+        for (int st = s0; st < s1; ++st) {
+            const uint32_t ctl = ldg(SD.ctrl + 4 * st + (lane >> 3));
+            const int A = SCH_A(ctl), B = SCH_B(ctl);
+            const float4 xa = X[8 * A + sl];
+            const float4 *rp = SD.rec4 + 256 * (size_t)st + lane;
+            const float *dp = SD.recd + 256 * (size_t)st + lane;
+            float ax = 0.f, ay = 0.f, az = 0.f, bx = 0.f, by = 0.f, bz = 0.f;
+#pragma unroll
+            for (int d = 0; d < 8; ++d) {
+                const float4 c = ldg(rp + 32 * d);
+                const float ds = ldg(dp + 32 * d);
+                const float4 xb = X[8 * B + ((sl + d) & 7)];
+                const float ddx = xa.x - xb.x, ddy = xa.y - xb.y, ddz = xa.z - xb.z;
+                const float r2 = fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz));
+                float s = 0.f;
+                if (r2 < kCut2) e += pair_energy<GRAD>(r2, c, ds, s);
+                if (GRAD) {
+                    const float fx = s * ddx, fy = s * ddy, fz = s * ddz;
+                    ax += fx; ay += fy; az += fz;
+                    bx = __shfl_sync(0xffffffffu, bx - fx, nxt);
+                    by = __shfl_sync(0xffffffffu, by - fy, nxt);
+                    bz = __shfl_sync(0xffffffffu, bz - fz, nxt);
                 }
+            }
+            if (GRAD && (ctl & SCH_VALID)) {
+                float4 pa = pq[8 * A + sl];
+                pa.x += ax; pa.y += ay; pa.z += az;
+                pq[8 * A + sl] = pa;
+                float4 pb = pq[8 * B + sl];
+                pb.x += bx; pb.y += by; pb.z += bz;
+                pq[8 * B + sl] = pb;
             }
         }
     }

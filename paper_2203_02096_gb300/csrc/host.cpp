@@ -355,82 +355,71 @@ struct Blob {
     }
 };
 
-// Systolic pair schedule for a team of W warps (see SchedDev): block pairs
-// holding at least one listed pair, assigned longest-first to the least
-// loaded of the 4W groups (lowest group on ties); each warp runs as many
-// rounds as its busiest group.  Pairs outside the list get zero records.
+// Systolic pair schedule for a team of W warps (see SchedDev): one step per
+// block pair holding at least one listed pair, dealt round-robin to the 4W
+// groups; each warp runs as many steps as its busiest group.
 struct SchedHost {
     std::vector<uint32_t> ctrl;
     std::vector<float4> rec4;
     std::vector<float> recd;
-    int base[8] = {0}, rounds[8] = {0};
-    long long listed = 0;  // non-zero pair slots (must equal the pair count)
+    int base[8] = {0}, steps[8] = {0};
+    double listed = 0;  // pair slots weighted 1 (0.5 on diagonal steps); must equal the pair count
 };
 
 SchedHost build_sched(int n, int W, const std::vector<int> &pidx, const std::vector<float4> &pc,
                       const std::vector<float> &pds) {
     const int nb = (n + 7) / 8, NG = 4 * W;
-    struct BP {
-        int A, B, rounds;
-    };
-    std::vector<BP> bps;
+    std::vector<std::pair<int, int>> bps;
     for (int A = 0; A < nb; ++A)
         for (int B = A; B < nb; ++B) {
             bool any = false;
             for (int a = 8 * A; a < 8 * A + 8 && a < n && !any; ++a)
                 for (int b = (A == B ? a + 1 : 8 * B); b < 8 * B + 8 && b < n && !any; ++b)
                     any = pidx[(size_t)a * n + b] >= 0;
-            if (any) bps.push_back({A, B, A == B ? 4 : 8});
+            if (any) bps.push_back({A, B});
         }
-    std::vector<int> order(bps.size());
-    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
-    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return bps[x].rounds > bps[y].rounds; });
     std::vector<std::vector<int>> glist(NG);
-    std::vector<int> load(NG, 0);
-    for (int idx : order) {
-        int g = 0;
-        for (int k = 1; k < NG; ++k)
-            if (load[k] < load[g]) g = k;
-        glist[g].push_back(idx);
-        load[g] += bps[idx].rounds;
-    }
+    for (size_t i = 0; i < bps.size(); ++i) glist[i % NG].push_back((int)i);
     SchedHost S;
     int off = 0;
     for (int w = 0; w < 8; ++w) {
         int R = 0;
         if (w < W)
-            for (int q = 0; q < 4; ++q) R = std::max(R, load[4 * w + q]);
+            for (int q = 0; q < 4; ++q) R = std::max(R, (int)glist[4 * w + q].size());
         S.base[w] = off;
-        S.rounds[w] = R;
+        S.steps[w] = R;
         off += R;
     }
-    S.ctrl.assign((size_t)std::max(off, 1) * 4, 0u);
-    S.rec4.assign((size_t)std::max(off, 1) * 32, make_float4(0.f, 0.f, 0.f, 0.f));
-    S.recd.assign((size_t)std::max(off, 1) * 32, 0.f);
+    const size_t ns = (size_t)std::max(off, 1);
+    S.ctrl.assign(ns * 4, 0u);
+    S.rec4.assign(ns * 256, make_float4(0.f, 0.f, 0.f, 0.f));
+    S.recd.assign(ns * 256, 0.f);
     for (int w = 0; w < W; ++w)
         for (int q = 0; q < 4; ++q) {
-            int round = S.base[w];
+            int st = S.base[w];
             for (int bi : glist[4 * w + q]) {
-                const BP &bp = bps[bi];
-                const bool diag = bp.A == bp.B;
-                for (int t = 0; t < bp.rounds; ++t, ++round) {
-                    const int d = diag ? t + 1 : t;
-                    uint32_t c = (uint32_t)bp.A | ((uint32_t)bp.B << 5) | ((uint32_t)d << 10) | SCH_VALID;
-                    if (t == 0) c |= SCH_FIRST;
-                    if (t == bp.rounds - 1) c |= SCH_LAST;
-                    if (diag) c |= SCH_DIAG;
-                    S.ctrl[4 * (size_t)round + q] = c;
+                const int A = bps[bi].first, B = bps[bi].second;
+                const bool diag = A == B;
+                S.ctrl[4 * (size_t)st + q] = (uint32_t)A | ((uint32_t)B << 5) | SCH_VALID;
+                for (int d = 0; d < 8; ++d)
                     for (int sl = 0; sl < 8; ++sl) {
-                        const int a = 8 * bp.A + sl, b = 8 * bp.B + ((sl + d) & 7);
-                        if (a >= n || b >= n || (diag && d == 4 && sl >= 4)) continue;
+                        const int a = 8 * A + sl, b = 8 * B + ((sl + d) & 7);
+                        if (a >= n || b >= n || a == b) continue;
                         const int i = std::min(a, b), j = std::max(a, b);
                         const int pp = pidx[(size_t)i * n + j];
                         if (pp < 0) continue;
-                        S.rec4[32 * (size_t)round + 8 * q + sl] = pc[pp];
-                        S.recd[32 * (size_t)round + 8 * q + sl] = pds[pp];
-                        ++S.listed;
+                        const size_t o = 256 * (size_t)st + 32 * d + 8 * q + sl;
+                        float4 c = pc[pp];
+                        float ds = pds[pp];
+                        if (diag) {  // met twice: half each time (exact in FP32)
+                            c.x *= 0.5f; c.y *= 0.5f; c.z *= 0.5f; c.w *= 0.5f;
+                            ds *= 0.5f;
+                        }
+                        S.rec4[o] = c;
+                        S.recd[o] = ds;
+                        S.listed += diag ? 0.5 : 1.0;
                     }
-                }
+                ++st;
             }
         }
     return S;
@@ -623,7 +612,7 @@ extern "C" int load_ligand(dock_ctx *ctx, int n, const double *xyz, const int *t
     SchedHost sched[4];
     for (int k = 0; k < 4; ++k) {
         sched[k] = build_sched(n, 1 << k, pidx, pc, pds);
-        if (sched[k].listed != P) return set_err(ctx, DOCK_ERR_INVALID, "internal error: pair schedule incomplete");
+        if (sched[k].listed != (double)P) return set_err(ctx, DOCK_ERR_INVALID, "internal error: pair schedule incomplete");
     }
     std::vector<std::vector<uint32_t>> lists(n);
     for (int p = 0; p < P; ++p) {
@@ -714,7 +703,7 @@ extern "C" int load_ligand(dock_ctx *ctx, int n, const double *xyz, const int *t
         d.sched[k].recd = (const float *)(base + o_srd[k]);
         for (int w = 0; w < 8; ++w) {
             d.sched[k].base[w] = sched[k].base[w];
-            d.sched[k].rounds[w] = sched[k].rounds[w];
+            d.sched[k].steps[w] = sched[k].steps[w];
         }
     }
     L->types = types;

@@ -17,26 +17,23 @@
 // entering fragment f are exactly the fragments [f, sub_end[f]).  Internal
 // torsion k is the bond entering fragment k+1.
 // Systolic pair schedule for a team of W warps (4W groups of 8 lanes).
-// Atoms form blocks of 8; a group processes a list of block pairs (A, B),
-// 8 rounds each (4 when A == B); in round d lane l pairs atom 8A + l with
-// atom 8B + (l + d) mod 8.  ctrl[round][group of the warp] packs A, B, d and
-// flags; rec4/recd[round][lane] hold the pair coefficients (c12, c6, c10,
-// qq) and the desolvation factor, zero for pairs outside the pair list.
+// Atoms form blocks of 8; a step is one block pair (A, B), 8 rounds: in
+// round d lane l of the group pairs atom 8A + l with atom 8B + (l + d) mod 8.
+// A diagonal step (A == B) meets every pair of its block twice (rounds d and
+// 8 - d), each time with half the coefficients.  ctrl[step][group of the
+// warp] packs A, B and a valid flag; rec4/recd[step][round][lane] hold the
+// coefficients (c12, c6, c10, qq) and the desolvation factor, zero for
+// pairs outside the pair list.
 struct SchedDev {
     const uint32_t *ctrl;
     const float4 *rec4;
     const float *recd;
-    int base[8];    // first round of warp w
-    int rounds[8];  // rounds of warp w
+    int base[8];   // first step of warp w
+    int steps[8];  // steps of warp w
 };
 
-// ctrl bit fields
 #define SCH_A(c) ((c) & 31u)
 #define SCH_B(c) (((c) >> 5) & 31u)
-#define SCH_D(c) (((c) >> 10) & 7u)
-#define SCH_FIRST 0x2000u
-#define SCH_LAST 0x4000u
-#define SCH_DIAG 0x8000u
 #define SCH_VALID 0x10000u
 
 struct LigandDev {
