@@ -177,10 +177,25 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
-// Sum over groups of k consecutive lanes (k a power of two <= 32).
-__device__ __forceinline__ float group_sum(float v, int k) {
-    for (int o = k >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
+// Sums over groups of 2^kl consecutive lanes, several values per level so
+// their shuffles overlap.
+__device__ __forceinline__ void group_sum3(float &a, float &b, float &c, int kl) {
+    for (int o = (1 << kl) >> 1; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+        c += __shfl_xor_sync(0xffffffffu, c, o);
+    }
+}
+
+__device__ __forceinline__ void group_sum6(float &a, float &b, float &c, float &d, float &e, float &f, int kl) {
+    for (int o = (1 << kl) >> 1; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+        c += __shfl_xor_sync(0xffffffffu, c, o);
+        d += __shfl_xor_sync(0xffffffffu, d, o);
+        e += __shfl_xor_sync(0xffffffffu, e, o);
+        f += __shfl_xor_sync(0xffffffffu, f, o);
+    }
 }
 
 // Team-wide sum, same bits on every thread: warp butterflies, then the warps'
@@ -202,11 +217,11 @@ __device__ __forceinline__ float team_sum(const Team<W> &tm, float v, float *red
     return s;
 }
 
-// Largest power of two k <= 32 with items * k <= team size (at least 1).
-__device__ __forceinline__ int lanes_per_item(int items, int team) {
-    int k = 1;
-    while (k < 32 && items * 2 * k <= team) k <<= 1;
-    return k;
+// log2 of the largest power of two k <= kmax with items * k <= team size.
+__device__ __forceinline__ int lanes_log2(int items, int team, int kmax) {
+    int kl = 0;
+    while ((2 << kl) <= kmax && items * (2 << kl) <= team) ++kl;
+    return kl;
 }
 
 // Evaluates the genotype stored at ws[Y.geno ...], which only warp 0 needs
@@ -244,8 +259,11 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
         float r00 = 0, r01 = 0, r02 = 0, r10 = 0, r11 = 0, r12 = 0, r20 = 0, r21 = 0, r22 = 0, t0 = 0, t1 = 0, t2 = 0;
         int depth = 0, parent = 0;
         if (lane < T) {
+            // reduce to [-pi, pi] (one multiple of 2 pi), then the fast intrinsic
+            float tau = geno[ldg(L.tors_gene + lane)];
+            tau = fmaf(-6.28318530717958647692f, rintf(tau * 0.15915494309189533577f), tau);
             float s, c;
-            sincosf(geno[ldg(L.tors_gene + lane)], &s, &c);
+            __sincosf(tau, &s, &c);
             const float4 u = ldg(L.tors_u + lane), b = ldg(L.tors_b + lane);
             const float oc = 1.f - c;
             r00 = fmaf(oc * u.x, u.x, c);        r01 = fmaf(oc * u.x, u.y, -s * u.z); r02 = fmaf(oc * u.x, u.z, s * u.y);
@@ -329,9 +347,14 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
                 const float4 xb = X[8 * B + ((sl + d) & 7)];
                 const float ddx = xa.x - xb.x, ddy = xa.y - xb.y, ddz = xa.z - xb.z;
                 const float r2 = fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz));
-                float s = 0.f;
-                if (r2 < kCut2) e += pair_energy<GRAD>(r2, c, ds, s);
+                // every round computes; the cutoff selects (one basic block for
+                // all 8 rounds, so they overlap)
+                float s;
+                const float ep = pair_energy<GRAD>(r2, c, ds, s);
+                const bool in = r2 < kCut2;
+                e += in ? ep : 0.f;
                 if (GRAD) {
+                    s = in ? s : 0.f;
                     const float fx = s * ddx, fy = s * ddy, fz = s * ddz;
                     ax += fx; ay += fy; az += fz;
                     bx = __shfl_sync(0xffffffffu, bx - fx, nxt);
@@ -362,15 +385,14 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
     if (!GRAD) return team_sum(tm, e, red);
     tm.sync();
 
-    // Per-atom force = grid part + the 4W group partials (k lanes per atom,
+    // Per-atom force = grid part + the 4W group partials (2^kl lanes per atom,
     // partials in group order, butterfly); torque (x_i - t) x f_i.
     float4 *Tq = reinterpret_cast<float4 *>(ws + Y.tq);
     {
         constexpr int NG = 4 * W;
-        const int k = lanes_per_item(N, S) < NG ? lanes_per_item(N, S) : NG;
-        const int per = S / k, sub = r & (k - 1);
-        for (int b0 = 0; b0 < N; b0 += per) {
-            const int i = b0 + r / k;
+        const int kl = lanes_log2(N, S, NG), k = 1 << kl, sub = r & (k - 1);
+        for (int b0 = 0; b0 < N; b0 += (S >> kl)) {
+            const int i = b0 + (r >> kl);
             const bool act = i < N;
             float fx = 0.f, fy = 0.f, fz = 0.f;
             if (act)
@@ -378,9 +400,7 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
                     const float4 v = PF[g * NB + i];
                     fx += v.x; fy += v.y; fz += v.z;
                 }
-            fx = group_sum(fx, k);
-            fy = group_sum(fy, k);
-            fz = group_sum(fz, k);
+            group_sum3(fx, fy, fz, kl);
             if (act && sub == 0) {
                 const float4 g = Fv[i], xi = X[i];
                 fx += g.x; fy += g.y; fz += g.z;
@@ -398,9 +418,9 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
     float4 *FS = reinterpret_cast<float4 *>(ws + Y.fs);
     const int F = L.n_frag;
     if (W == 1) {
-        const int m = lanes_per_item(F, S), per = S / m, sub = r & (m - 1);
-        for (int b0 = 0; b0 < F; b0 += per) {
-            const int f = b0 + r / m;
+        const int ml = lanes_log2(F, S, 32), m = 1 << ml, sub = r & (m - 1);
+        for (int b0 = 0; b0 < F; b0 += (S >> ml)) {
+            const int f = b0 + (r >> ml);
             const bool act = f < F;
             int lo = 0, hi = 0;
             if (act) {
@@ -414,8 +434,7 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
                 a0 += fv.x; a1 += fv.y; a2 += fv.z;
                 a3 += t.x; a4 += t.y; a5 += t.z;
             }
-            a0 = group_sum(a0, m); a1 = group_sum(a1, m); a2 = group_sum(a2, m);
-            a3 = group_sum(a3, m); a4 = group_sum(a4, m); a5 = group_sum(a5, m);
+            group_sum6(a0, a1, a2, a3, a4, a5, ml);
             if (act && sub == 0) {
                 FS[2 * f] = make_float4(a0, a1, a2, 0.f);
                 FS[2 * f + 1] = make_float4(a3, a4, a5, 0.f);
@@ -425,9 +444,9 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
     }
     float *grad = ws + Y.grad;
     {
-        const int R = T + 1, m = lanes_per_item(R, S), per = S / m, sub = r & (m - 1);
-        for (int b0 = 0; b0 < R; b0 += per) {
-            const int k = b0 + r / m;
+        const int R = T + 1, ml = lanes_log2(R, S, 32), m = 1 << ml, sub = r & (m - 1);
+        for (int b0 = 0; b0 < R; b0 += (S >> ml)) {
+            const int k = b0 + (r >> ml);
             const bool act = k < R;
             int lo = 0, hi = 0;
             if (act) {
@@ -448,8 +467,7 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
                 a0 += u.x; a1 += u.y; a2 += u.z;
                 a3 += v.x; a4 += v.y; a5 += v.z;
             }
-            a0 = group_sum(a0, m); a1 = group_sum(a1, m); a2 = group_sum(a2, m);
-            a3 = group_sum(a3, m); a4 = group_sum(a4, m); a5 = group_sum(a5, m);
+            group_sum6(a0, a1, a2, a3, a4, a5, ml);
             if (act && sub == 0) {
                 if (k < T) {  // u_k . sum over the moved atoms of (x_i - x_b) x f_i
                     const int2 ab = ldg(L.tors_ab + k);
