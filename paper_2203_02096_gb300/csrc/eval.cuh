@@ -147,24 +147,32 @@ __device__ __forceinline__ float atom_grid_energy(const GridDev &G, const AtomCe
     return fmaf(aq, vd, fmaf(q, ve, vt)) + A.c.pen;
 }
 
-// Intramolecular pair: energy, and s = (dE/dr)/r (0 below the floor), for
-// squared distance r2 < 64.
+// Intramolecular pair: energy, and s = (dE/dr)/r (0 below the floor).
+// c = (c12, cn, qq, ds): vdW pairs carry cn = c6 >= 0 (E = c12/r^12 -
+// c6/r^6), H-bond pairs cn = -c10 < 0 (E = c12/r^12 - c10/r^10);
+// qq = w_el 332.06 q_i q_j; ds = w_ds (S_i V_j + S_j V_i).
 template <bool GRAD>
-__device__ __forceinline__ float pair_energy(float r2, float4 c, float ds, float &s) {
+__device__ __forceinline__ float pair_energy(float r2, float4 c, float &s) {
     const float r2e = fmaxf(r2, kFloor2);
     const float rinv = rsqrtf(r2e);
     const float r = r2e * rinv;
-    const float ri2 = rinv * rinv, ri6 = ri2 * ri2 * ri2, ri10 = ri6 * ri2 * ri2, ri12 = ri6 * ri6;
-    const float ev = c.x * ri12 - c.y * ri6 - c.z * ri10;
+    const float ri2 = rinv * rinv, ri6 = ri2 * ri2 * ri2, ri12 = ri6 * ri6;
+    const bool hb = c.y < 0.f;
+    const float rk = hb ? ri6 * ri2 * ri2 : ri6;  // r^-10 or r^-6
+    const float cn = fabsf(c.y);
+    const float ev = fmaf(c.x, ri12, -cn * rk);
+    // sigmoidal dielectric eps = A + B / (1 + k exp(-lambda B r))
     const float ex = __expf(-kDielLB * r);
-    const float den = fmaf(kDielK, ex, 1.f);
-    const float eps = kDielA + __fdividef(kDielB, den);
-    const float eel = c.w * __fdividef(rinv, eps);
-    const float eds = ds * __expf(-r2e * kHalfInvSig2);
+    const float inv_den = __fdividef(1.f, fmaf(kDielK, ex, 1.f));
+    const float eps = fmaf(kDielB, inv_den, kDielA);
+    const float inv_eps = __fdividef(1.f, eps);
+    const float eel = c.z * rinv * inv_eps;
+    const float eds = c.w * __expf(-r2e * kHalfInvSig2);
     if (GRAD) {
-        const float dv = (-12.f * c.x * ri12 + 6.f * c.y * ri6 + 10.f * c.z * ri10) * rinv;
-        const float deps = __fdividef(kDielDeps * ex, den * den);
-        const float del = -eel * __fdividef(fmaf(r, deps, eps), eps * r);
+        const float dv = fmaf(-12.f * c.x, ri12, (hb ? 10.f : 6.f) * cn * rk) * rinv;
+        // eps' / eps with eps' = B k lambda B e / (1 + k e)^2
+        const float deps_eps = kDielDeps * ex * inv_den * inv_den * inv_eps;
+        const float del = -eel * (rinv + deps_eps);  // d(qq / (eps r)) / dr
         const float dds = -eds * r * kInvSig2;
         s = r2 >= kFloor2 ? (dv + del + dds) * rinv : 0.f;
     }
@@ -238,6 +246,9 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
     float4 *PF = reinterpret_cast<float4 *>(ws + Y.pf);
     float *red = ws + Y.red;
     const int T = L.n_tors, N = L.n_atoms, NB = L.nb8;
+    // item i of a per-atom (or per-range) phase goes to warp i mod W, so the
+    // team's warps share the work evenly: first item of this thread
+    const int i0 = lane * W + tm.warp();
 
     // Warp 0: rigid-body transform and the torsion tree, one level at a time
     // (M_child = M_parent o L_k; torsion k is lane k < 32).
@@ -296,7 +307,7 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
     tm.sync();
 
     // Atom positions relative to t (padding atoms up to a multiple of 8 at 0).
-    for (int i = r; i < NB; i += S) {
+    for (int i = i0; i < NB; i += S) {
         float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
         if (i < N) {
             const float4 p = ldg(L.ref + i);
@@ -316,9 +327,9 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
     const float tux = (tx - G.ox) * G.inv_h, tuy = (ty - G.oy) * G.inv_h, tuz = (tz - G.oz) * G.inv_h;
     float4 *Fv = reinterpret_cast<float4 *>(ws + Y.f);
     AtomCells A0;
-    if (r < N) {
-        const float4 xi = X[r];
-        atom_fetch(G, ldg(G.map_of_type + (ldg(L.meta + r) & 255)), ldg(L.ref + r).w, fmaf(xi.x, G.inv_h, tux),
+    if (i0 < N) {
+        const float4 xi = X[i0];
+        atom_fetch(G, ldg(G.map_of_type + (ldg(L.meta + i0) & 255)), ldg(L.ref + i0).w, fmaf(xi.x, G.inv_h, tux),
                    fmaf(xi.y, G.inv_h, tuy), fmaf(xi.z, G.inv_h, tuz), A0);
     }
 
@@ -337,20 +348,18 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
             const uint32_t ctl = ldg(SD.ctrl + 4 * st + (lane >> 3));
             const int A = SCH_A(ctl), B = SCH_B(ctl);
             const float4 xa = X[8 * A + sl];
-            const float4 *rp = SD.rec4 + 256 * (size_t)st + lane;
-            const float *dp = SD.recd + 256 * (size_t)st + lane;
+            const float4 *rp = SD.rec + 256 * (size_t)st + lane;
             float ax = 0.f, ay = 0.f, az = 0.f, bx = 0.f, by = 0.f, bz = 0.f;
 #pragma unroll
             for (int d = 0; d < 8; ++d) {
                 const float4 c = ldg(rp + 32 * d);
-                const float ds = ldg(dp + 32 * d);
                 const float4 xb = X[8 * B + ((sl + d) & 7)];
                 const float ddx = xa.x - xb.x, ddy = xa.y - xb.y, ddz = xa.z - xb.z;
                 const float r2 = fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz));
                 // every round computes; the cutoff selects (one basic block for
                 // all 8 rounds, so they overlap)
                 float s;
-                const float ep = pair_energy<GRAD>(r2, c, ds, s);
+                const float ep = pair_energy<GRAD>(r2, c, s);
                 const bool in = r2 < kCut2;
                 e += in ? ep : 0.f;
                 if (GRAD) {
@@ -372,8 +381,8 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
             }
         }
     }
-    for (int i = r; i < N; i += S) {
-        if (i != r) {
+    for (int i = i0; i < N; i += S) {
+        if (i != i0) {
             const float4 xi = X[i];
             atom_fetch(G, ldg(G.map_of_type + (ldg(L.meta + i) & 255)), ldg(L.ref + i).w, fmaf(xi.x, G.inv_h, tux),
                        fmaf(xi.y, G.inv_h, tuy), fmaf(xi.z, G.inv_h, tuz), A0);
@@ -392,7 +401,7 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
         constexpr int NG = 4 * W;
         const int kl = lanes_log2(N, S, NG), k = 1 << kl, sub = r & (k - 1);
         for (int b0 = 0; b0 < N; b0 += (S >> kl)) {
-            const int i = b0 + (r >> kl);
+            const int i = b0 + ((lane >> kl) * W + tm.warp());
             const bool act = i < N;
             float fx = 0.f, fy = 0.f, fz = 0.f;
             if (act)
@@ -446,7 +455,7 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
     {
         const int R = T + 1, ml = lanes_log2(R, S, 32), m = 1 << ml, sub = r & (m - 1);
         for (int b0 = 0; b0 < R; b0 += (S >> ml)) {
-            const int k = b0 + (r >> ml);
+            const int k = b0 + ((lane >> ml) * W + tm.warp());
             const bool act = k < R;
             int lo = 0, hi = 0;
             if (act) {

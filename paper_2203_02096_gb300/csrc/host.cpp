@@ -360,14 +360,12 @@ struct Blob {
 // groups; each warp runs as many steps as its busiest group.
 struct SchedHost {
     std::vector<uint32_t> ctrl;
-    std::vector<float4> rec4;
-    std::vector<float> recd;
+    std::vector<float4> rec;
     int base[8] = {0}, steps[8] = {0};
     double listed = 0;  // pair slots weighted 1 (0.5 on diagonal steps); must equal the pair count
 };
 
-SchedHost build_sched(int n, int W, const std::vector<int> &pidx, const std::vector<float4> &pc,
-                      const std::vector<float> &pds) {
+SchedHost build_sched(int n, int W, const std::vector<int> &pidx, const std::vector<float4> &pc) {
     const int nb = (n + 7) / 8, NG = 4 * W;
     std::vector<std::pair<int, int>> bps;
     for (int A = 0; A < nb; ++A)
@@ -392,8 +390,7 @@ SchedHost build_sched(int n, int W, const std::vector<int> &pidx, const std::vec
     }
     const size_t ns = (size_t)std::max(off, 1);
     S.ctrl.assign(ns * 4, 0u);
-    S.rec4.assign(ns * 256, make_float4(0.f, 0.f, 0.f, 0.f));
-    S.recd.assign(ns * 256, 0.f);
+    S.rec.assign(ns * 256, make_float4(0.f, 0.f, 0.f, 0.f));
     for (int w = 0; w < W; ++w)
         for (int q = 0; q < 4; ++q) {
             int st = S.base[w];
@@ -410,13 +407,10 @@ SchedHost build_sched(int n, int W, const std::vector<int> &pidx, const std::vec
                         if (pp < 0) continue;
                         const size_t o = 256 * (size_t)st + 32 * d + 8 * q + sl;
                         float4 c = pc[pp];
-                        float ds = pds[pp];
                         if (diag) {  // met twice: half each time (exact in FP32)
                             c.x *= 0.5f; c.y *= 0.5f; c.z *= 0.5f; c.w *= 0.5f;
-                            ds *= 0.5f;
                         }
-                        S.rec4[o] = c;
-                        S.recd[o] = ds;
+                        S.rec[o] = c;
                         S.listed += diag ? 0.5 : 1.0;
                     }
                 ++st;
@@ -590,7 +584,6 @@ extern "C" int load_ligand(dock_ctx *ctx, int n, const double *xyz, const int *t
     // pair list: different rigid fragments, >= 4 bonds apart
     std::vector<uint32_t> pij;
     std::vector<float4> pc;
-    std::vector<float> pds;
     std::vector<double> pc64;
     for (int i = 0; i < n; ++i)
         for (int j = i + 1; j < n; ++j) {
@@ -602,8 +595,8 @@ extern "C" int load_ligand(dock_ctx *ctx, int n, const double *xyz, const int *t
             const double ds = ff::kWds * (ff::solv(type[I], charge[I]) * ff::kTypes[type[J]].vol +
                                           ff::solv(type[J], charge[J]) * ff::kTypes[type[I]].vol);
             pij.push_back((uint32_t)i | ((uint32_t)j << 16));
-            pc.push_back(make_float4((float)c12, (float)c6, (float)c10, (float)qq));
-            pds.push_back((float)ds);
+            // c6 and c10 are never both non-zero: the sign of cn selects the exponent
+            pc.push_back(make_float4((float)c12, c10 != 0.0 ? -(float)c10 : (float)c6, (float)qq, (float)ds));
             pc64.insert(pc64.end(), {c12, c6, c10, qq, ds});
         }
     const int P = (int)pij.size();
@@ -611,7 +604,7 @@ extern "C" int load_ligand(dock_ctx *ctx, int n, const double *xyz, const int *t
     for (int p = 0; p < P; ++p) pidx[(size_t)(pij[p] & 0xffff) * n + (pij[p] >> 16)] = p;
     SchedHost sched[4];
     for (int k = 0; k < 4; ++k) {
-        sched[k] = build_sched(n, 1 << k, pidx, pc, pds);
+        sched[k] = build_sched(n, 1 << k, pidx, pc);
         if (sched[k].listed != (double)P) return set_err(ctx, DOCK_ERR_INVALID, "internal error: pair schedule incomplete");
     }
     std::vector<std::vector<uint32_t>> lists(n);
@@ -643,17 +636,15 @@ extern "C" int load_ligand(dock_ctx *ctx, int n, const double *xyz, const int *t
     const size_t o_trg = B.add(trange.data(), T * sizeof(int2));
     const size_t o_pij = B.add(pij.data(), P * sizeof(uint32_t));
     const size_t o_pc = B.add(pc.data(), P * sizeof(float4));
-    const size_t o_pds = B.add(pds.data(), P * sizeof(float));
     const size_t o_aoff = B.add(adj_off.data(), (n + 1) * sizeof(int));
     const size_t o_adj = B.add(adjv.data(), adjv.size() * sizeof(uint32_t));
     const size_t o_r64 = B.add(ref64.data(), 3 * n * sizeof(double));
     const size_t o_pc64 = B.add(pc64.data(), pc64.size() * sizeof(double));
     const size_t o_q64 = B.add(q64.data(), n * sizeof(double));
-    size_t o_sc[4], o_sr4[4], o_srd[4];
+    size_t o_sc[4], o_sr[4];
     for (int k = 0; k < 4; ++k) {
         o_sc[k] = B.add(sched[k].ctrl.data(), sched[k].ctrl.size() * sizeof(uint32_t));
-        o_sr4[k] = B.add(sched[k].rec4.data(), sched[k].rec4.size() * sizeof(float4));
-        o_srd[k] = B.add(sched[k].recd.data(), sched[k].recd.size() * sizeof(float));
+        o_sr[k] = B.add(sched[k].rec.data(), sched[k].rec.size() * sizeof(float4));
     }
 
     dock_ligand *L = new dock_ligand();
@@ -690,7 +681,6 @@ extern "C" int load_ligand(dock_ctx *ctx, int n, const double *xyz, const int *t
     d.tors_range = (const int2 *)(base + o_trg);
     d.pair_ij = (const uint32_t *)(base + o_pij);
     d.pair_c = (const float4 *)(base + o_pc);
-    d.pair_ds = (const float *)(base + o_pds);
     d.adj_off = (const int *)(base + o_aoff);
     d.adj = (const uint32_t *)(base + o_adj);
     d.ref64 = (const double *)(base + o_r64);
@@ -699,8 +689,7 @@ extern "C" int load_ligand(dock_ctx *ctx, int n, const double *xyz, const int *t
     d.nb8 = (n + 7) & ~7;
     for (int k = 0; k < 4; ++k) {
         d.sched[k].ctrl = (const uint32_t *)(base + o_sc[k]);
-        d.sched[k].rec4 = (const float4 *)(base + o_sr4[k]);
-        d.sched[k].recd = (const float *)(base + o_srd[k]);
+        d.sched[k].rec = (const float4 *)(base + o_sr[k]);
         for (int w = 0; w < 8; ++w) {
             d.sched[k].base[w] = sched[k].base[w];
             d.sched[k].steps[w] = sched[k].steps[w];

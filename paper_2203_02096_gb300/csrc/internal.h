@@ -21,13 +21,12 @@
 // round d lane l of the group pairs atom 8A + l with atom 8B + (l + d) mod 8.
 // A diagonal step (A == B) meets every pair of its block twice (rounds d and
 // 8 - d), each time with half the coefficients.  ctrl[step][group of the
-// warp] packs A, B and a valid flag; rec4/recd[step][round][lane] hold the
-// coefficients (c12, c6, c10, qq) and the desolvation factor, zero for
-// pairs outside the pair list.
+// warp] packs A, B and a valid flag; rec[step][round][lane] holds the pair
+// coefficients (c12, cn, qq, ds) -- cn = c6 for 12-6 pairs, -c10 for 12-10
+// H-bond pairs -- zero for pairs outside the pair list.
 struct SchedDev {
     const uint32_t *ctrl;
-    const float4 *rec4;
-    const float *recd;
+    const float4 *rec;
     int base[8];   // first step of warp w
     int steps[8];  // steps of warp w
 };
@@ -51,8 +50,7 @@ struct LigandDev {
     const int2 *tors_ab;      // [T] internal atom indices (a, b)
     const int *tors_gene;     // [T] genotype index of internal torsion k
     const uint32_t *pair_ij;  // [P] i | j << 16, internal atom indices
-    const float4 *pair_c;     // [P] (c12, c6, c10, w_el * 332.06 * q_i q_j)
-    const float *pair_ds;     // [P] w_ds (S_i V_j + S_j V_i)
+    const float4 *pair_c;     // [P] (c12, cn, w_el * 332.06 * q_i q_j, w_ds (S_i V_j + S_j V_i)), cn as above
     const int *adj_off;       // [n+1] CSR over atoms of the pairs they take part in
     const uint32_t *adj;      // [2P] pair index | partner atom << 16
     const double *ref64;      // [n][3] centred reference coords (FP64 re-score)
