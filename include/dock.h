@@ -175,6 +175,24 @@ int dock(dock_ctx *ctx, const dock_grids *grids, const dock_ligand *lig, const d
 int dock_async(dock_ctx *ctx, const dock_grids *grids, const dock_ligand *lig, const dock_params *params,
                uint64_t seed, float *best_geno, float *best_E32, double *best_E, int64_t *evals_used, void *stream);
 
+/* ---- many ligands in one persistent launch ----
+ * Docks n_ligs ligands against the same grids: every run of every ligand is
+ * one task and one warp runs a whole task (all generations, children,
+ * scores and local searches, the same operators and stream layout as
+ * dock()), claiming tasks from a device counter, largest ligands first, so
+ * ligands of uneven size share one launch.  seeds[k] (host, may be NULL =
+ * k) keys ligand k's random stream.  Device outputs, row t = k * nruns + r:
+ * best_geno [n_ligs*nruns][39] (genes 0..G_k-1 used, unit quaternion),
+ * best_E32 [n_ligs*nruns] (may be NULL), best_E [n_ligs*nruns] (FP64
+ * re-score), evals_used [n_ligs*nruns] (may be NULL).  Blocks until done.
+ * A run's result depends only on its ligand, run index, seed and params, not
+ * on the other ligands of the batch; it uses one-warp evaluation, so its
+ * values may differ in the last bits from dock(), which spreads a local
+ * search over several warps when runs are few. */
+int dock_batch(dock_ctx *ctx, const dock_grids *grids, const dock_ligand *const *ligs, int n_ligs,
+               const dock_params *params, const uint64_t *seeds, float *best_geno, float *best_E32, double *best_E,
+               int64_t *evals_used, void *stream);
+
 /* ---- docking without device allocation ----
  * Not a step of the paper's method (it has no counterpart there): the same
  * docking as dock_async -- same kernels, same results for the same inputs --

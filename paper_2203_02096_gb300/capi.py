@@ -64,6 +64,7 @@ SIGNATURES = {
     "dock": (_i, [_vp, _vp, _vp, _P(DockParams), _u64, _vp, _vp, _vp]),
     "dock_async": (_i, [_vp, _vp, _vp, _P(DockParams), _u64, _vp, _vp, _vp, _vp, _vp]),
     "dock_async_noalloc": (_i, [_vp, _vp, _vp, _P(DockParams), _u64, _vp, _vp, _vp, _vp, _vp]),
+    "dock_batch": (_i, [_vp, _vp, _vp, _i, _P(DockParams), _vp, _vp, _vp, _vp, _vp, _vp]),
     "dock_init_population": (_i, [_vp, _vp, _i, _i, _i, _u64, _vp, _vp]),
     "dock_ga_children": (_i, [_vp, _i, _i, _i, _vp, _vp, _u64, _u32, _P(DockParams), _vp, _vp, _vp]),
     "dock_ls_picks": (_i, [_vp, _i, _i, _i, _u64, _u32, _vp, _vp]),
@@ -328,6 +329,27 @@ def dock_async_noalloc(ctx: Context, grids: Grids, lig: Ligand, params: DockPara
     ctx.check(ctx.lib.dock_async_noalloc(ctx.h, grids.h, lig.h, C.byref(params), int(seed), _ptr(out["best_geno"]),
                                          _ptr(out["best_E32"]), _ptr(out["best_E"]), _ptr(out["evals"]),
                                          _stream(stream)), "dock_async_noalloc")
+    return out
+
+
+GENE_STRIDE = 39   # 7 + maximum torsions: row stride of dock_batch's best_geno
+
+
+def dock_batch(ctx: Context, grids: Grids, ligs, params: DockParams, seeds=None, stream=None):
+    """Dock many ligands in one persistent launch.  Returns device tensors
+    best_geno [n, nruns, 39], best_E32 [n, nruns], best_E [n, nruns] (FP64),
+    evals [n, nruns]; ligand k uses genes [:, :, :ligs[k].n_genes]."""
+    n, R = len(ligs), params.nruns
+    dev = torch.device("cuda", ctx.device)
+    out = dict(best_geno=torch.zeros((n, R, GENE_STRIDE), dtype=torch.float32, device=dev),
+               best_E32=torch.empty((n, R), dtype=torch.float32, device=dev),
+               best_E=torch.empty((n, R), dtype=torch.float64, device=dev),
+               evals=torch.empty((n, R), dtype=torch.int64, device=dev))
+    arr = (C.c_void_p * max(n, 1))(*[l.h for l in ligs])
+    sd = None if seeds is None else np.ascontiguousarray(seeds, dtype=np.uint64)
+    ctx.check(ctx.lib.dock_batch(ctx.h, grids.h, arr, n, C.byref(params), _ptr(sd) if sd is not None else None,
+                                 _ptr(out["best_geno"]), _ptr(out["best_E32"]), _ptr(out["best_E"]),
+                                 _ptr(out["evals"]), _stream(stream)), "dock_batch")
     return out
 
 
