@@ -301,9 +301,15 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
             }
         }
     }
-    // Per-group force partials start at zero.
-    if (GRAD)
-        for (int k = r; k < 4 * W * NB; k += S) PF[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    // Force accumulators start at zero: W = 1 adds pair forces straight into
+    // the per-atom forces, W > 1 into per-group partials.
+    float4 *Fv = reinterpret_cast<float4 *>(ws + Y.f);
+    if (GRAD) {
+        if (W == 1)
+            for (int k = r; k < NB; k += S) Fv[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        else
+            for (int k = r; k < 4 * W * NB; k += S) PF[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
     tm.sync();
 
     // Atom positions relative to t (padding atoms up to a multiple of 8 at 0).
@@ -325,7 +331,6 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
     // rounds run while they are in flight.
     const float tx = geno[0], ty = geno[1], tz = geno[2];
     const float tux = (tx - G.ox) * G.inv_h, tuy = (ty - G.oy) * G.inv_h, tuz = (tz - G.oz) * G.inv_h;
-    float4 *Fv = reinterpret_cast<float4 *>(ws + Y.f);
     AtomCells A0;
     if (i0 < N) {
         const float4 xi = X[i0];
@@ -342,7 +347,7 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
         const SchedDev &SD = L.sched[W == 1 ? 0 : W == 2 ? 1 : W == 4 ? 2 : 3];
         const int w = tm.warp(), q = 4 * w + (lane >> 3), sl = lane & 7, gb = lane & ~7;
         const int nxt = gb | ((sl + 1) & 7);
-        float4 *pq = PF + q * NB;
+        float4 *pq = W == 1 ? Fv : PF + q * NB;  // W = 1: the step's groups touch disjoint atoms
         const int s0 = SD.base[w], s1 = s0 + SD.steps[w];
         for (int st = s0; st < s1; ++st) {
             const uint32_t ctl = ldg(SD.ctrl + 4 * st + (lane >> 3));
@@ -379,8 +384,11 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
                 pb.x += bx; pb.y += by; pb.z += bz;
                 pq[8 * B + sl] = pb;
             }
+            // W = 1: the next step may give these atoms to another group
+            if (GRAD && W == 1) __syncwarp();
         }
     }
+    if (W == 1 && GRAD) __syncwarp();  // pair forces in Fv before the grid part is added
     for (int i = i0; i < N; i += S) {
         if (i != i0) {
             const float4 xi = X[i];
@@ -389,15 +397,29 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
         }
         float3 g;
         e += atom_grid_energy<GRAD>(G, A0, g);
-        if (GRAD) Fv[i] = make_float4(g.x, g.y, g.z, 0.f);
+        if (GRAD) {
+            if (W == 1) {
+                float4 f = Fv[i];
+                f.x += g.x; f.y += g.y; f.z += g.z;
+                Fv[i] = f;
+            } else {
+                Fv[i] = make_float4(g.x, g.y, g.z, 0.f);
+            }
+        }
     }
     if (!GRAD) return team_sum(tm, e, red);
     tm.sync();
 
     // Per-atom force = grid part + the 4W group partials (2^kl lanes per atom,
-    // partials in group order, butterfly); torque (x_i - t) x f_i.
+    // partials in group order, butterfly); torque (x_i - t) x f_i.  W = 1:
+    // the forces are complete already.
     float4 *Tq = reinterpret_cast<float4 *>(ws + Y.tq);
-    {
+    if (W == 1) {
+        for (int i = r; i < N; i += S) {
+            const float4 f = Fv[i], xi = X[i];
+            Tq[i] = make_float4(xi.y * f.z - xi.z * f.y, xi.z * f.x - xi.x * f.z, xi.x * f.y - xi.y * f.x, 0.f);
+        }
+    } else {
         constexpr int NG = 4 * W;
         const int kl = lanes_log2(N, S, NG), k = 1 << kl, sub = r & (k - 1);
         for (int b0 = 0; b0 < N; b0 += (S >> kl)) {

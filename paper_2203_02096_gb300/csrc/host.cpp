@@ -356,8 +356,11 @@ struct Blob {
 };
 
 // Systolic pair schedule for a team of W warps (see SchedDev): one step per
-// block pair holding at least one listed pair, dealt round-robin to the 4W
-// groups; each warp runs as many steps as its busiest group.
+// block pair holding at least one listed pair.  W = 1: steps are matchings
+// (the warp's 4 groups touch disjoint blocks), so the warp can add pair forces
+// straight into per-atom forces; W > 1: block pairs dealt round-robin to the
+// 4W groups, each with its own partial forces.  Each warp runs as many steps
+// as its busiest group.
 struct SchedHost {
     std::vector<uint32_t> ctrl;
     std::vector<float4> rec;
@@ -377,7 +380,26 @@ SchedHost build_sched(int n, int W, const std::vector<int> &pidx, const std::vec
             if (any) bps.push_back({A, B});
         }
     std::vector<std::vector<int>> glist(NG);
-    for (size_t i = 0; i < bps.size(); ++i) glist[i % NG].push_back((int)i);
+    if (W == 1) {
+        // one warp accumulates straight into per-atom forces: the 4 block pairs
+        // of a step must touch disjoint blocks (greedy matchings, in order)
+        std::vector<char> done(bps.size(), 0);
+        size_t left = bps.size();
+        while (left) {
+            std::vector<char> used(nb, 0);
+            int q = 0;
+            for (size_t i = 0; i < bps.size() && q < 4; ++i) {
+                if (done[i] || used[bps[i].first] || used[bps[i].second]) continue;
+                used[bps[i].first] = used[bps[i].second] = 1;
+                done[i] = 1;
+                --left;
+                glist[q++].push_back((int)i);
+            }
+            for (; q < 4; ++q) glist[q].push_back(-1);  // idle group this step
+        }
+    } else {
+        for (size_t i = 0; i < bps.size(); ++i) glist[i % NG].push_back((int)i);
+    }
     SchedHost S;
     int off = 0;
     for (int w = 0; w < 8; ++w) {
@@ -395,6 +417,10 @@ SchedHost build_sched(int n, int W, const std::vector<int> &pidx, const std::vec
         for (int q = 0; q < 4; ++q) {
             int st = S.base[w];
             for (int bi : glist[4 * w + q]) {
+                if (bi < 0) {  // idle: valid flag clear, zero records
+                    ++st;
+                    continue;
+                }
                 const int A = bps[bi].first, B = bps[bi].second;
                 const bool diag = A == B;
                 S.ctrl[4 * (size_t)st + q] = (uint32_t)A | ((uint32_t)B << 5) | SCH_VALID;

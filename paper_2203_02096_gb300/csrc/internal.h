@@ -91,9 +91,9 @@ __host__ __device__ inline EvalLayout eval_layout(int n_atoms, int n_frag, int n
     w.M = o; o += 12 * n_frag;
     w.fs = o; o += grad ? 8 * n_frag : 0;
     w.x = o; o += 4 * nb8;
-    w.f = o; o += grad ? 4 * n_atoms : 0;
+    w.f = o; o += grad ? 4 * nb8 : 0;
     w.tq = o; o += grad ? 4 * n_atoms : 0;
-    w.pf = o; o += grad ? 4 * 4 * W * nb8 : 0;
+    w.pf = o; o += (grad && W > 1) ? 4 * 4 * W * nb8 : 0;  // W = 1 adds straight into f
     w.total = round4(o);
     return w;
 }
