@@ -382,7 +382,36 @@ SchedHost build_sched(int n, int W, const std::vector<int> &pidx, const std::vec
     std::vector<std::vector<int>> glist(NG);
     if (W == 1) {
         // one warp accumulates straight into per-atom forces: the 4 block pairs
-        // of a step must touch disjoint blocks (greedy matchings, in order)
+        // of a step must touch disjoint blocks.  Order the block pairs by the
+        // rounds of a round-robin tournament over the blocks (circle method:
+        // each round is a perfect matching; a block paired with the padding
+        // block gets its diagonal pair), then pack greedily, 4 per step.
+        {
+            const int ne = nb + (nb & 1);
+            std::vector<std::pair<int, int>> order;
+            std::vector<char> diag_done(nb, 0);
+            for (int rr = 0; rr < ne - 1; ++rr) {
+                std::vector<int> arr(ne);
+                arr[0] = ne - 1;
+                for (int i = 1; i < ne; ++i) arr[i] = (rr + i - 1) % (ne - 1);
+                for (int i = 0; i < ne / 2; ++i) {
+                    int a = arr[i], b = arr[ne - 1 - i];
+                    if (a > b) std::swap(a, b);
+                    if (b >= nb) {
+                        order.push_back({a, a});
+                        diag_done[a] = 1;
+                    } else {
+                        order.push_back({a, b});
+                    }
+                }
+            }
+            for (int d = 0; d < nb; ++d)
+                if (!diag_done[d]) order.push_back({d, d});
+            std::vector<std::pair<int, int>> keep;
+            for (const auto &e : order)
+                if (std::find(bps.begin(), bps.end(), e) != bps.end()) keep.push_back(e);
+            bps = keep;
+        }
         std::vector<char> done(bps.size(), 0);
         size_t left = bps.size();
         while (left) {
