@@ -43,6 +43,7 @@ extern "C" {
 #define DOCK_ERR_TYPE (-7)         /* unknown atom type code                       */
 #define DOCK_ERR_NOMAP (-8)        /* a ligand atom type has no map in the grids   */
 #define DOCK_ERR_DEVICE (-9)       /* a kernel reported an error through its flag  */
+#define DOCK_ERR_BUSY (-10)        /* the serving queue has no free slot right now */
 
 #define DOCK_MAX_ATOMS 255
 #define DOCK_MAX_TORSIONS 32
@@ -142,6 +143,8 @@ int load_ligand(dock_ctx *ctx, int n_atoms, const double *xyz, const int *type, 
 int ligand_info(const dock_ligand *lig, int *n_atoms, int *n_torsions, int *n_genes, int *n_pairs,
                 int *n_fragments);
 int free_ligand(dock_ctx *ctx, dock_ligand *lig);
+/* Device bytes a loaded ligand holds (for admission by device memory). */
+int ligand_device_bytes(const dock_ligand *lig, size_t *bytes);
 
 /* ---- batched evaluation (spec: score_batch, score_grad_batch) ----
  * geno: device [B][G] FP32.  E: device [B] FP32 energies (kcal/mol).
@@ -192,6 +195,35 @@ int dock_async(dock_ctx *ctx, const dock_grids *grids, const dock_ligand *lig, c
 int dock_batch(dock_ctx *ctx, const dock_grids *grids, const dock_ligand *const *ligs, int n_ligs,
                const dock_params *params, const uint64_t *seeds, float *best_geno, float *best_E32, double *best_E,
                int64_t *evals_used, void *stream);
+
+/* ---- serving: continuous batching of docking requests ----
+ * A server keeps a persistent docking kernel fed from a queue: each request
+ * (one ligand, its grids, params and seed) becomes nruns tasks; warps of the
+ * running kernel pick tasks up as soon as they are submitted, so requests of
+ * different sizes arriving while others run share the GPU at once.  The
+ * queue lives in mapped host memory; idle warps poll it with a bounded wait
+ * and leave after about a second without work; server_submit and
+ * server_poll relaunch the kernel when tasks are pending and none runs.  A
+ * task's result depends only on its ligand, grids, params, seed and run
+ * index (the same as dock_batch for them), not on what else is queued.
+ * server_create: capacity = task slots (results of a task stay readable
+ * until capacity more tasks have been submitted), max_atoms = largest
+ * ligand accepted, pop_max = largest pop_size accepted.
+ * server_submit: the ligand and grids must stay loaded until the request is
+ * done; returns the request's first task number; DOCK_ERR_BUSY when the
+ * slots it would reuse are still running.
+ * server_poll: *done = 1 once all nruns tasks from first_task are finished.
+ * server_result: host outputs best_geno [nruns][n_genes], best_E [nruns]
+ * (FP64 re-score), evals_used [nruns] (each may be NULL).
+ * server_destroy: asks the warps to leave, waits for them, frees. */
+typedef struct dock_server dock_server;
+int server_create(dock_ctx *ctx, int capacity, int max_atoms, int pop_max, dock_server **out);
+int server_submit(dock_server *srv, const dock_grids *grids, const dock_ligand *lig, const dock_params *params,
+                  uint64_t seed, int64_t *first_task);
+int server_poll(dock_server *srv, int64_t first_task, int nruns, int *done);
+int server_result(dock_server *srv, int64_t first_task, int nruns, int n_genes, float *best_geno, double *best_E,
+                  int64_t *evals_used);
+int server_destroy(dock_server *srv);
 
 /* ---- docking without device allocation ----
  * Not a step of the paper's method (it has no counterpart there): the same

@@ -22,7 +22,9 @@ _lib = None
 
 DOCK_OK = 0
 ERRORS = {-1: "DOCK_ERR_INVALID", -2: "DOCK_ERR_CUDA", -3: "DOCK_ERR_OOM", -4: "DOCK_ERR_DISCONNECTED",
-          -5: "DOCK_ERR_RING", -6: "DOCK_ERR_SIZE", -7: "DOCK_ERR_TYPE", -8: "DOCK_ERR_NOMAP", -9: "DOCK_ERR_DEVICE"}
+          -5: "DOCK_ERR_RING", -6: "DOCK_ERR_SIZE", -7: "DOCK_ERR_TYPE", -8: "DOCK_ERR_NOMAP", -9: "DOCK_ERR_DEVICE",
+          -10: "DOCK_ERR_BUSY"}
+DOCK_ERR_BUSY = -10
 MAP_ELEC, MAP_DESOLV = -1, -2
 
 # Every symbol include/dock.h declares, with (restype, argtypes).
@@ -58,6 +60,7 @@ SIGNATURES = {
     "load_ligand": (_i, [_vp, _i, _vp, _vp, _vp, _i, _vp, _vp, _P(_vp)]),
     "ligand_info": (_i, [_vp, _P(_i), _P(_i), _P(_i), _P(_i), _P(_i)]),
     "free_ligand": (_i, [_vp, _vp]),
+    "ligand_device_bytes": (_i, [_vp, _P(_sz)]),
     "score_batch": (_i, [_vp, _vp, _vp, _vp, _i, _vp, _vp]),
     "score_grad_batch": (_i, [_vp, _vp, _vp, _vp, _i, _vp, _vp, _vp]),
     "pose_batch": (_i, [_vp, _vp, _vp, _i, _vp, _vp]),
@@ -65,6 +68,11 @@ SIGNATURES = {
     "dock_async": (_i, [_vp, _vp, _vp, _P(DockParams), _u64, _vp, _vp, _vp, _vp, _vp]),
     "dock_async_noalloc": (_i, [_vp, _vp, _vp, _P(DockParams), _u64, _vp, _vp, _vp, _vp, _vp]),
     "dock_batch": (_i, [_vp, _vp, _vp, _i, _P(DockParams), _vp, _vp, _vp, _vp, _vp, _vp]),
+    "server_create": (_i, [_vp, _i, _i, _i, _P(_vp)]),
+    "server_submit": (_i, [_vp, _vp, _vp, _P(DockParams), _u64, _P(_i64)]),
+    "server_poll": (_i, [_vp, _i64, _i, _P(_i)]),
+    "server_result": (_i, [_vp, _i64, _i, _i, _vp, _vp, _vp]),
+    "server_destroy": (_i, [_vp]),
     "dock_init_population": (_i, [_vp, _vp, _i, _i, _i, _u64, _vp, _vp]),
     "dock_ga_children": (_i, [_vp, _i, _i, _i, _vp, _vp, _u64, _u32, _P(DockParams), _vp, _vp, _vp]),
     "dock_ls_picks": (_i, [_vp, _i, _i, _i, _u64, _u32, _vp, _vp]),
@@ -245,6 +253,11 @@ class Ligand:
         ctx.check(ctx.lib.ligand_info(h, *[C.byref(x) for x in v]), "ligand_info")
         self.n_atoms, self.n_torsions, self.n_genes, self.n_pairs, self.n_fragments = (x.value for x in v)
 
+    def device_bytes(self) -> int:
+        b = C.c_size_t()
+        self.ctx.check(self.ctx.lib.ligand_device_bytes(self.h, C.byref(b)), "ligand_device_bytes")
+        return int(b.value)
+
     def free(self):
         if self.h is not None and self.ctx.h is not None:
             self.ctx.lib.free_ligand(self.ctx.h, self.h)
@@ -351,6 +364,49 @@ def dock_batch(ctx: Context, grids: Grids, ligs, params: DockParams, seeds=None,
                                  _ptr(out["best_geno"]), _ptr(out["best_E32"]), _ptr(out["best_E"]),
                                  _ptr(out["evals"]), _stream(stream)), "dock_batch")
     return out
+
+
+class Server:
+    """Continuous-batching docking server (server_* in dock.h)."""
+
+    def __init__(self, ctx: Context, capacity: int = 65536, max_atoms: int = 128, pop_max: int = 150):
+        self.ctx = ctx
+        h = C.c_void_p()
+        ctx.check(ctx.lib.server_create(ctx.h, capacity, max_atoms, pop_max, C.byref(h)), "server_create")
+        self.h = h
+
+    def submit(self, grids: Grids, lig: Ligand, params: DockParams, seed: int):
+        """Returns the first task number, or None when the queue is full."""
+        t = C.c_int64()
+        rc = self.ctx.lib.server_submit(self.h, grids.h, lig.h, C.byref(params), int(seed), C.byref(t))
+        if rc == DOCK_ERR_BUSY:
+            return None
+        self.ctx.check(rc, "server_submit")
+        return t.value
+
+    def done(self, first_task: int, nruns: int) -> bool:
+        d = C.c_int()
+        self.ctx.check(self.ctx.lib.server_poll(self.h, int(first_task), int(nruns), C.byref(d)), "server_poll")
+        return bool(d.value)
+
+    def result(self, first_task: int, nruns: int, n_genes: int):
+        g = np.zeros((nruns, n_genes), dtype=np.float32)
+        e = np.zeros(nruns, dtype=np.float64)
+        v = np.zeros(nruns, dtype=np.int64)
+        self.ctx.check(self.ctx.lib.server_result(self.h, int(first_task), int(nruns), int(n_genes), _ptr(g), _ptr(e),
+                                                  _ptr(v)), "server_result")
+        return g, e, v
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.ctx.h is not None:
+            self.ctx.lib.server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def dock_init_population(ctx, grids, n_torsions, pop, nruns, seed, stream=None):

@@ -14,6 +14,7 @@
 
 #include <algorithm>
 #include <numeric>
+#include <string.h>
 #include <vector>
 
 #include "ga.cuh"
@@ -274,3 +275,321 @@ extern "C" int dock_batch(dock_ctx *ctx, const dock_grids *grids, const dock_lig
     if (!best_E32) dev_free(ctx, bE32, s);
     return rc;
 }
+
+// ---------------------------------------------------------------------------
+// Serving: the same warp-per-run docking fed from a live queue.  Requests
+// become tasks in a ring that lives in mapped (zero-copy) host memory; the
+// host publishes a tail count, idle warps poll it with a bounded wait and
+// exit when no work arrives for a while (the host relaunches the kernel when
+// new work comes).  No kernel waits on another kernel.
+
+namespace {
+
+struct ServeTask {
+    LigandDev lig;
+    GridDev grid;
+    BatchConst P;
+    unsigned long long seed;
+    int run, out;
+};
+
+struct ServeCtl {
+    long long tail;  // tasks published (host writes)
+    int stop;        // host asks every warp to leave
+    int pad;
+};
+
+// Copies a trivially copyable struct from (mapped host) memory into shared
+// memory with the warp's lanes.
+template <typename T>
+__device__ __forceinline__ void warp_copy(T *dst, const volatile T *src, int lane) {
+    static_assert(sizeof(T) % 4 == 0, "word copy");
+    const volatile uint32_t *s = reinterpret_cast<const volatile uint32_t *>(src);
+    uint32_t *d = reinterpret_cast<uint32_t *>(dst);
+    for (int i = lane; i < (int)(sizeof(T) / 4); i += 32) d[i] = s[i];
+}
+
+__global__ void __launch_bounds__(128, 4)
+lga_serve(const volatile ServeTask *tasks, const volatile ServeCtl *ctl, int capacity, unsigned long long *head,
+          float *scratch, size_t floats_per_warp, int pop_max, size_t smem_per_warp, float *best_geno,
+          float *best_E32, double *best_E, unsigned long long *evals, volatile long long *done,
+          long long max_idle_polls) {
+    extern __shared__ float4 smem4[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int gw = blockIdx.x * (blockDim.x >> 5) + wib;
+    // per warp: the task's descriptors, then the evaluator's scratch
+    const size_t desc_floats = (sizeof(ServeTask) + 15) / 16 * 4;
+    float *base = reinterpret_cast<float *>(smem4) + wib * (smem_per_warp + desc_floats);
+    ServeTask *T = reinterpret_cast<ServeTask *>(base);
+    float *ws = base + desc_floats;
+    for (;;) {
+        long long t = -1;
+        if (lane == 0) {
+            for (long long polls = 0;; ++polls) {
+                if (ctl->stop) break;
+                const long long h = (long long)atomicAdd(head, 0ull);
+                const long long tail = ctl->tail;
+                if (h < tail) {
+                    if ((long long)atomicCAS(head, (unsigned long long)h, (unsigned long long)(h + 1)) == h) {
+                        t = h;
+                        break;
+                    }
+                    continue;
+                }
+                if (polls >= max_idle_polls) break;  // bounded: idle warps leave
+                __nanosleep(20000);
+            }
+        }
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t < 0) break;
+        __threadfence_system();  // the task record was written before tail
+        warp_copy(T, tasks + (t % capacity), lane);
+        __syncwarp();
+        const LigandDev &L = T->lig;
+        const GridDev &G = T->grid;
+        const BatchConst &P = T->P;
+        GaConst C;
+        C.pop = P.pop;
+        C.nruns = 1;
+        C.nt = L.n_tors;
+        C.p_tour = P.p_tour;
+        C.p_cross = P.p_cross;
+        C.p_mut = P.p_mut;
+        C.trans_mut = P.trans_mut;
+        C.key = make_uint2((uint32_t)T->seed, (uint32_t)(T->seed >> 32));
+        const EvalLayout Yn = eval_layout(L.n_atoms, L.n_frag, L.nb8, false, 1);
+        const EvalLayout Yg = eval_layout(L.n_atoms, L.n_frag, L.nb8, true, 1);
+        const WarpScratch S = warp_scratch(scratch, floats_per_warp, gw, pop_max, 7 + DOCK_MAX_TORSIONS);
+        const int out = T->out;
+        const long long ev = dock_run_warp(L, G, C, P, ws, Yn, Yg, S, T->run, best_geno + (size_t)out * P.gstride,
+                                           best_E32 + out);
+        __syncwarp();
+        if (lane == 0) {
+            best_E[out] = rescore64_one(L, G, best_geno + (size_t)out * P.gstride);
+            evals[out] = (unsigned long long)ev;
+            __threadfence_system();
+            done[out] = t + 1;  // completion: the task's sequence number
+        }
+        __syncwarp();
+    }
+}
+
+}  // namespace
+
+struct dock_server {
+    dock_ctx *ctx = nullptr;
+    cudaStream_t stream = nullptr;
+    int capacity = 0, max_atoms = 0, pop_max = 0, warps = 0, wpb = 0, blocks = 0;
+    size_t smem_per_warp = 0, smem = 0, floats_per_warp = 0;
+    ServeTask *tasks = nullptr;  // mapped host
+    ServeCtl *ctl = nullptr;     // mapped host
+    long long *done = nullptr;   // mapped host
+    ServeTask *d_tasks = nullptr;
+    ServeCtl *d_ctl = nullptr;
+    long long *d_done = nullptr;
+    unsigned long long *head = nullptr;
+    float *scratch = nullptr, *best_geno = nullptr, *best_E32 = nullptr;
+    double *best_E = nullptr;
+    unsigned long long *evals = nullptr;
+    long long submitted = 0;
+    cudaEvent_t running = nullptr;  // recorded after each launch
+    bool launched = false;
+};
+
+extern "C" {
+
+int server_create(dock_ctx *ctx, int capacity, int max_atoms, int pop_max, dock_server **out) {
+    if (!ctx || !out) return DOCK_ERR_INVALID;
+    *out = nullptr;
+    if (capacity < 1 || capacity > (1 << 22) || max_atoms < 1 || max_atoms > DOCK_MAX_ATOMS || pop_max < 2 ||
+        pop_max > 4096)
+        return set_err(ctx, DOCK_ERR_INVALID, "server_create: capacity, max_atoms or pop_max out of range");
+    dock_server *S = new dock_server();
+    S->ctx = ctx;
+    S->capacity = capacity;
+    S->max_atoms = max_atoms;
+    S->pop_max = pop_max;
+    const int nb8 = (max_atoms + 7) & ~7;
+    S->smem_per_warp = (size_t)eval_layout(max_atoms, DOCK_MAX_TORSIONS + 1, nb8, true, 1).total;
+    const size_t desc_floats = (sizeof(ServeTask) + 15) / 16 * 4;
+    const size_t per_warp_bytes = (S->smem_per_warp + desc_floats) * 4;
+    S->wpb = 4;
+    while (S->wpb > 1 && per_warp_bytes * S->wpb > ctx->smem_optin) S->wpb >>= 1;
+    if (per_warp_bytes > ctx->smem_optin) {
+        delete S;
+        return set_err(ctx, DOCK_ERR_SIZE, "server_create: max_atoms too large for shared memory");
+    }
+    S->smem = per_warp_bytes * S->wpb;
+    cudaError_t e = cudaSuccess;
+    if (S->smem > 48 * 1024) e = cudaFuncSetAttribute(lga_serve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S->smem);
+    int per_sm = 0;
+    if (!e) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lga_serve, 32 * S->wpb, S->smem);
+    if (e || per_sm < 1) {
+        delete S;
+        return e ? cuda_err(ctx, e, "server_create occupancy") : set_err(ctx, DOCK_ERR_SIZE, "no occupancy");
+    }
+    S->blocks = per_sm * ctx->num_sms;
+    S->warps = S->blocks * S->wpb;
+    const int gmax = 7 + DOCK_MAX_TORSIONS;
+    S->floats_per_warp = ((2 * (size_t)pop_max * gmax + 3 * (size_t)pop_max + 63) / 64) * 64;
+    e = cudaHostAlloc((void **)&S->tasks, sizeof(ServeTask) * capacity, cudaHostAllocMapped);
+    if (!e) e = cudaHostAlloc((void **)&S->ctl, sizeof(ServeCtl), cudaHostAllocMapped);
+    if (!e) e = cudaHostAlloc((void **)&S->done, sizeof(long long) * capacity, cudaHostAllocMapped);
+    if (!e) e = cudaHostGetDevicePointer((void **)&S->d_tasks, S->tasks, 0);
+    if (!e) e = cudaHostGetDevicePointer((void **)&S->d_ctl, S->ctl, 0);
+    if (!e) e = cudaHostGetDevicePointer((void **)&S->d_done, S->done, 0);
+    if (!e) e = cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking);
+    if (!e) e = cudaEventCreateWithFlags(&S->running, cudaEventDisableTiming);
+    if (e) {
+        server_destroy(S);
+        return cuda_err(ctx, e, "server_create host buffers");
+    }
+    memset(S->ctl, 0, sizeof(ServeCtl));
+    memset(S->done, 0, sizeof(long long) * capacity);
+    S->head = (unsigned long long *)dev_alloc(ctx, 8, S->stream);
+    S->scratch = (float *)dev_alloc(ctx, S->floats_per_warp * 4 * S->warps, S->stream);
+    S->best_geno = (float *)dev_alloc(ctx, (size_t)capacity * gmax * 4, S->stream);
+    S->best_E32 = (float *)dev_alloc(ctx, (size_t)capacity * 4, S->stream);
+    S->best_E = (double *)dev_alloc(ctx, (size_t)capacity * 8, S->stream);
+    S->evals = (unsigned long long *)dev_alloc(ctx, (size_t)capacity * 8, S->stream);
+    if (!S->head || !S->scratch || !S->best_geno || !S->best_E32 || !S->best_E || !S->evals) {
+        server_destroy(S);
+        return set_err(ctx, DOCK_ERR_OOM, "server_create device buffers");
+    }
+    e = cudaMemsetAsync(S->head, 0, 8, S->stream);
+    if (!e) e = cudaStreamSynchronize(S->stream);
+    if (e) {
+        server_destroy(S);
+        return cuda_err(ctx, e, "server_create");
+    }
+    *out = S;
+    return DOCK_OK;
+}
+
+// (Re)launches the persistent kernel when none is running.
+static int server_kick(dock_server *S) {
+    if (S->launched && cudaEventQuery(S->running) == cudaErrorNotReady) return DOCK_OK;
+    cudaGetLastError();
+    const long long max_idle = 50000;  // x 20 us: an idle warp leaves after about a second
+    lga_serve<<<S->blocks, 32 * S->wpb, S->smem, S->stream>>>(
+        S->d_tasks, S->d_ctl, S->capacity, S->head, S->scratch, S->floats_per_warp, S->pop_max, S->smem_per_warp,
+        S->best_geno, S->best_E32, S->best_E, S->evals, S->d_done, max_idle);
+    ++S->ctx->launches;
+    cudaError_t e = cudaGetLastError();
+    if (!e) e = cudaEventRecord(S->running, S->stream);
+    if (e) return cuda_err(S->ctx, e, "server launch");
+    S->launched = true;
+    return DOCK_OK;
+}
+
+int server_submit(dock_server *S, const dock_grids *grids, const dock_ligand *lig, const dock_params *params,
+                  uint64_t seed, int64_t *first_task) {
+    if (!S || !grids || !lig || !first_task) return S ? set_err(S->ctx, DOCK_ERR_INVALID, "null argument") : DOCK_ERR_INVALID;
+    dock_ctx *ctx = S->ctx;
+    dock_params P;
+    if (params) P = *params;
+    else dock_default_params(&P);
+    if (P.ls_count < 0) P.ls_count = (6 * P.pop_size + 99) / 100;
+    if (P.pop_size < 2 || P.pop_size > S->pop_max || P.nruns < 1 || P.nruns > S->capacity || P.max_evals < 0 ||
+        P.ls_count > P.pop_size || P.ls_iters < 0 || !(P.rho >= 0.f && P.rho < 1.f) || !(P.eps > 0.f))
+        return set_err(ctx, DOCK_ERR_INVALID, "server_submit: invalid dock_params");
+    if (lig->dev.n_atoms > S->max_atoms) return set_err(ctx, DOCK_ERR_SIZE, "server_submit: ligand above max_atoms");
+    int rc = check_maps(ctx, grids, lig);
+    if (rc) return rc;
+    // room: the oldest slot reused must be done
+    const long long first = S->submitted, last = first + P.nruns - 1;
+    for (long long t = std::max(0LL, first - S->capacity); t <= last - S->capacity; ++t)
+        if (*(volatile long long *)&S->done[t % S->capacity] != t + 1)
+            return set_err(ctx, DOCK_ERR_BUSY, "server_submit: queue full");
+    BatchConst BC;
+    BC.pop = P.pop_size;
+    BC.n_ls = P.ls_count;
+    BC.iters = P.ls_iters;
+    const long long per_gen = (long long)(P.pop_size - 1) + (long long)P.ls_count * P.ls_iters;
+    BC.ngen = P.max_evals > P.pop_size ? (P.max_evals - P.pop_size + per_gen - 1) / per_gen : 0;
+    BC.rho = P.rho;
+    BC.eps = P.eps;
+    BC.p_tour = P.p_tour;
+    BC.p_cross = P.p_cross;
+    BC.p_mut = P.p_mut;
+    BC.trans_mut = P.trans_mut;
+    BC.gstride = 7 + DOCK_MAX_TORSIONS;
+    for (int r = 0; r < P.nruns; ++r) {
+        const long long t = first + r;
+        ServeTask &T = S->tasks[t % S->capacity];
+        T.lig = lig->dev;
+        T.grid = grids->dev;
+        T.P = BC;
+        T.seed = seed;
+        T.run = r;
+        T.out = (int)(t % S->capacity);
+    }
+    S->submitted = last + 1;
+    __atomic_thread_fence(__ATOMIC_SEQ_CST);
+    *(volatile long long *)&S->ctl->tail = S->submitted;  // publish
+    __atomic_thread_fence(__ATOMIC_SEQ_CST);
+    *first_task = first;
+    return server_kick(S);
+}
+
+int server_poll(dock_server *S, int64_t first_task, int nruns, int *done) {
+    if (!S || !done || nruns < 1) return S ? set_err(S->ctx, DOCK_ERR_INVALID, "invalid argument") : DOCK_ERR_INVALID;
+    int all = 1;
+    for (int r = 0; r < nruns && all; ++r) {
+        const long long t = first_task + r;
+        all = *(volatile long long *)&S->done[t % S->capacity] == t + 1;
+    }
+    *done = all;
+    if (!all) return server_kick(S);  // keep the kernel alive while work is pending
+    return DOCK_OK;
+}
+
+int server_result(dock_server *S, int64_t first_task, int nruns, int n_genes, float *best_geno, double *best_E,
+                  int64_t *evals_used) {
+    if (!S || nruns < 1 || n_genes < 7 || n_genes > 7 + DOCK_MAX_TORSIONS)
+        return S ? set_err(S->ctx, DOCK_ERR_INVALID, "invalid argument") : DOCK_ERR_INVALID;
+    const int gmax = 7 + DOCK_MAX_TORSIONS;
+    std::vector<float> g((size_t)gmax);
+    for (int r = 0; r < nruns; ++r) {
+        const long long t = first_task + r;
+        const int slot = (int)(t % S->capacity);
+        if (*(volatile long long *)&S->done[slot] != t + 1) return set_err(S->ctx, DOCK_ERR_INVALID, "result not ready");
+        cudaError_t e = cudaSuccess;
+        if (best_geno) {
+            e = cudaMemcpy(g.data(), S->best_geno + (size_t)slot * gmax, gmax * 4, cudaMemcpyDeviceToHost);
+            memcpy(best_geno + (size_t)r * n_genes, g.data(), n_genes * 4);
+        }
+        if (!e && best_E) e = cudaMemcpy(best_E + r, S->best_E + slot, 8, cudaMemcpyDeviceToHost);
+        if (!e && evals_used) {
+            unsigned long long v = 0;
+            e = cudaMemcpy(&v, S->evals + slot, 8, cudaMemcpyDeviceToHost);
+            evals_used[r] = (int64_t)v;
+        }
+        if (e) return cuda_err(S->ctx, e, "server_result");
+    }
+    return DOCK_OK;
+}
+
+int server_destroy(dock_server *S) {
+    if (!S) return DOCK_ERR_INVALID;
+    if (S->ctl) *(volatile int *)&S->ctl->stop = 1;
+    __atomic_thread_fence(__ATOMIC_SEQ_CST);
+    if (S->stream) cudaStreamSynchronize(S->stream);  // warps leave at their next claim
+    dock_ctx *ctx = S->ctx;
+    dev_free(ctx, S->head, S->stream);
+    dev_free(ctx, S->scratch, S->stream);
+    dev_free(ctx, S->best_geno, S->stream);
+    dev_free(ctx, S->best_E32, S->stream);
+    dev_free(ctx, S->best_E, S->stream);
+    dev_free(ctx, S->evals, S->stream);
+    if (S->stream) cudaStreamSynchronize(S->stream);
+    if (S->tasks) cudaFreeHost(S->tasks);
+    if (S->ctl) cudaFreeHost(S->ctl);
+    if (S->done) cudaFreeHost(S->done);
+    if (S->running) cudaEventDestroy(S->running);
+    if (S->stream) cudaStreamDestroy(S->stream);
+    delete S;
+    return DOCK_OK;
+}
+
+}  // extern "C"

@@ -767,6 +767,12 @@ int ligand_info(const dock_ligand *l, int *n_atoms, int *n_torsions, int *n_gene
     return DOCK_OK;
 }
 
+int ligand_device_bytes(const dock_ligand *l, size_t *bytes) {
+    if (!l || !bytes) return DOCK_ERR_INVALID;
+    *bytes = l->blob_bytes;
+    return DOCK_OK;
+}
+
 int free_ligand(dock_ctx *ctx, dock_ligand *l) {
     if (!ctx || !l) return DOCK_ERR_INVALID;
     cudaStreamSynchronize(nullptr);

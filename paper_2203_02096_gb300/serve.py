@@ -1,0 +1,111 @@
+"""Request loop of the docking service: continuous batching over server_*.
+
+Requests (a ligand, a receptor's grids, a seed) arrive over time; each is
+admitted as soon as the device memory it needs -- its ligand data and its
+result rows -- fits the budget and the server has free task slots, and is
+then submitted to the running persistent kernel, where its runs share the
+GPU with whatever else is in flight.  Completed requests release their
+memory at once.  Reports per-request latency (arrival to all runs done)
+and throughput.
+"""
+from __future__ import annotations
+
+import time
+from collections import deque
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import capi
+
+ROW_BYTES = 4 * capi.GENE_STRIDE + 4 + 8 + 8   # result row of one run on the device
+
+
+@dataclass
+class Request:
+    ligand: object          # synth.Ligand
+    grid_index: int
+    seed: int
+    arrival: float = 0.0    # seconds from the start of the run
+
+
+@dataclass
+class Done:
+    request: Request
+    latency: float
+    best_geno: np.ndarray
+    best_E: np.ndarray
+    evals: np.ndarray
+
+
+@dataclass
+class ServiceReport:
+    done: list = field(default_factory=list)
+    wall: float = 0.0
+    max_in_flight: int = 0
+
+    def latencies(self) -> np.ndarray:
+        return np.array([d.latency for d in self.done])
+
+    def summary(self) -> dict:
+        lat = self.latencies()
+        return {"requests": len(self.done), "wall_s": self.wall,
+                "throughput_per_s": len(self.done) / self.wall if self.wall > 0 else 0.0,
+                "ligands_per_hour": 3600.0 * len(self.done) / self.wall if self.wall > 0 else 0.0,
+                "p50_s": float(np.percentile(lat, 50)) if len(lat) else None,
+                "p99_s": float(np.percentile(lat, 99)) if len(lat) else None,
+                "max_in_flight": self.max_in_flight}
+
+
+def poisson_arrivals(n: int, rate: float, seed: int = 0) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    return np.cumsum(rng.exponential(1.0 / rate, size=n))
+
+
+def run(ctx: capi.Context, server: capi.Server, grids: list, requests: list, params: capi.DockParams,
+        mem_budget: int = 2 << 30, poll_sleep: float = 2e-4, timeout: float = 600.0) -> ServiceReport:
+    """Serve ``requests`` (their ``arrival`` times set) until all are done."""
+    pending = deque(sorted(requests, key=lambda r: r.arrival))
+    waiting = deque()          # arrived, not yet admitted
+    in_flight = []             # (request, ligand handle, first task, bytes)
+    used = 0
+    rep = ServiceReport()
+    t0 = time.perf_counter()
+    while pending or waiting or in_flight:
+        now = time.perf_counter() - t0
+        if now > timeout:
+            raise TimeoutError(f"service did not finish within {timeout} s")
+        while pending and pending[0].arrival <= now:
+            waiting.append(pending.popleft())
+        # admission: device memory budget and free task slots, in arrival order
+        while waiting:
+            req = waiting[0]
+            lig = capi.ligand_from(ctx, req.ligand)
+            need = lig.device_bytes() + params.nruns * ROW_BYTES
+            if in_flight and used + need > mem_budget:
+                lig.free()
+                break
+            first = server.submit(grids[req.grid_index], lig, params, req.seed)
+            if first is None:   # no free slots yet
+                lig.free()
+                break
+            waiting.popleft()
+            in_flight.append((req, lig, first, need))
+            used += need
+        rep.max_in_flight = max(rep.max_in_flight, len(in_flight))
+        still = []
+        for req, lig, first, need in in_flight:
+            if server.done(first, params.nruns):
+                g, e, v = server.result(first, params.nruns, lig.n_genes)
+                rep.done.append(Done(req, time.perf_counter() - t0 - req.arrival, g, e, v))
+                lig.free()
+                used -= need
+            else:
+                still.append((req, lig, first, need))
+        in_flight = still
+        if in_flight or waiting:
+            time.sleep(poll_sleep)
+        elif pending:
+            time.sleep(max(0.0, min(pending[0].arrival - (time.perf_counter() - t0), 0.01)))
+    rep.wall = time.perf_counter() - t0
+    return rep
