@@ -300,6 +300,7 @@ def run(args):
 
     batch = score_grad_throughput(ctx, G, w.box, dev) if not args.no_batch else None
     multi = batched_docking(ctx, dev) if not args.no_batch else None
+    serving = serving_sweep(ctx, dev) if not args.no_batch else None
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -329,6 +330,7 @@ def run(args):
             "cpu_baseline": cpu,
             "score_grad_batch": batch,
             "batched_docking": multi,
+            "serving": serving,
             "best_energy_median": float(np.median(out["best_E"].cpu().numpy())),
         }
         print(json.dumps(line), flush=True)
@@ -425,6 +427,60 @@ def batched_docking(ctx, dev, n_ligs: int = 1024, nruns: int = 20, evals_per_run
             "batched_ligands_per_hour_extrapolated": 3600.0 * rate_b / per_lig_full,
             "plain_ligands_per_hour_extrapolated": 3600.0 * rate_p / per_lig_full,
             "batch_seconds": t_batch, "launches": 1}
+
+
+def serving_sweep(ctx, dev, rates=(10, 30, 100, 300, 1000), seconds: float = 2.0, nruns: int = 20,
+                  evals_per_run: int = 5_000, full_budget: int = 500_000, n_plain: int = 8):
+    """Continuous-batching service (server_* + serve.run): Poisson arrivals
+    of ligands with 10-128 atoms (log-uniform) and 0-32 torsions against two
+    receptors with 96^3 x 9 maps, 20 runs per request; p50/p99 latency and
+    throughput per arrival rate, beside the plain form (one dock() call per
+    request, in arrival order).  Each run gets evals_per_run evaluations
+    (full budget 500k: latencies scale with it, the ordering does not)."""
+    import torch
+
+    from paper_2203_02096_gb300 import capi, serve, synth
+    centers = [(12.5, -3.25, 7.0), (-30.0, 18.0, 4.0)]
+    grids = [capi.grids_from_receptor(ctx, synth.make_receptor(3000, center=c, seed=11 + i), synth.make_box(96, center=c))
+             for i, c in enumerate(centers)]
+    P = capi.default_params(pop_size=150, nruns=nruns, max_evals=evals_per_run, ls_iters=100)
+    server = capi.Server(ctx, capacity=1 << 16, max_atoms=128, pop_max=150)
+    rng = np.random.default_rng(17)
+
+    def request(k):
+        n = int(np.exp(rng.uniform(np.log(10), np.log(128.999))))
+        return serve.Request(synth.make_ligand(n, int(rng.integers(0, 33)), seed=9000 + k), k % 2, seed=k)
+
+    # warm-up: one request through the server
+    serve.run(ctx, server, grids, [request(0)], P)
+    out = []
+    for rate in rates:
+        n = max(8, int(rate * seconds))
+        reqs = [request(k) for k in range(n)]
+        for r, t in zip(reqs, serve.poisson_arrivals(n, rate, seed=int(rate))):
+            r.arrival = float(t)
+        rep = serve.run(ctx, server, grids, reqs, P)
+        out.append(dict(rate_per_s=rate, **rep.summary()))
+    # the plain form: one docking at a time
+    reqs = [request(k) for k in range(n_plain)]
+    t0 = time.perf_counter()
+    lat = []
+    for r in reqs:
+        ts = time.perf_counter()
+        L = capi.ligand_from(ctx, r.ligand)
+        capi.dock(ctx, grids[r.grid_index], L, P, r.seed)
+        L.free()
+        lat.append(time.perf_counter() - ts)
+    t_plain = time.perf_counter() - t0
+    server.close()
+    for g in grids:
+        g.free()
+    torch.cuda.synchronize(dev)
+    return {"workload": "ligands 10-128 atoms (log-uniform), 0-32 torsions, 20 runs, 2 receptors x 96^3 x 9 maps",
+            "sample": f"{evals_per_run} evaluations per run (full budget {full_budget}); {seconds} s of arrivals per rate",
+            "sweep": out,
+            "plain": {"requests_per_s": n_plain / t_plain, "ligands_per_hour": 3600.0 * n_plain / t_plain,
+                      "latency_s_median": float(np.median(lat))}}
 
 
 def pair_list(lig):
