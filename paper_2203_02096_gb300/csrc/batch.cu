@@ -299,6 +299,26 @@ struct ServeCtl {
     int pad;
 };
 
+// Device-side queue state. Only the warp that wins the refresh slot reads the
+// host's mapped control block (at most once per kRefreshNs), so idle warps
+// poll L2 instead of the host link.
+struct ServeDev {
+    unsigned long long head;         // next task to claim
+    unsigned long long tail;         // copy of the host's published tail
+    unsigned long long last_read;    // globaltimer of the last host read
+    unsigned long long last_active;  // globaltimer of the last claim
+    unsigned long long stop;         // copy of the host's stop flag
+};
+
+constexpr long long kMaxPolls = 100000000;
+constexpr unsigned long long kRefreshNs = 4000;
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 // Copies a trivially copyable struct from (mapped host) memory into shared
 // memory with the warp's lanes.
 template <typename T>
@@ -310,10 +330,10 @@ __device__ __forceinline__ void warp_copy(T *dst, const volatile T *src, int lan
 }
 
 __global__ void __launch_bounds__(128, 4)
-lga_serve(const volatile ServeTask *tasks, const volatile ServeCtl *ctl, int capacity, unsigned long long *head,
+lga_serve(const volatile ServeTask *tasks, const volatile ServeCtl *ctl, int capacity, ServeDev *q,
           float *scratch, size_t floats_per_warp, int pop_max, size_t smem_per_warp, float *best_geno,
           float *best_E32, double *best_E, unsigned long long *evals, volatile long long *done,
-          long long max_idle_polls) {
+          unsigned long long max_idle_ns) {
     extern __shared__ float4 smem4[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int gw = blockIdx.x * (blockDim.x >> 5) + wib;
@@ -325,19 +345,30 @@ lga_serve(const volatile ServeTask *tasks, const volatile ServeCtl *ctl, int cap
     for (;;) {
         long long t = -1;
         if (lane == 0) {
+            volatile ServeDev *vq = q;
+            const unsigned long long idle0 = globaltimer_ns();
             for (long long polls = 0;; ++polls) {
-                if (ctl->stop) break;
-                const long long h = (long long)atomicAdd(head, 0ull);
-                const long long tail = ctl->tail;
-                if (h < tail) {
-                    if ((long long)atomicCAS(head, (unsigned long long)h, (unsigned long long)(h + 1)) == h) {
+                if (vq->stop) break;
+                const long long h = (long long)vq->head;
+                if (h < (long long)vq->tail) {
+                    if ((long long)atomicCAS(&q->head, (unsigned long long)h, (unsigned long long)(h + 1)) == h) {
+                        atomicMax(&q->last_active, globaltimer_ns());
                         t = h;
                         break;
                     }
                     continue;
                 }
-                if (polls >= max_idle_polls) break;  // bounded: idle warps leave
-                __nanosleep(20000);
+                const unsigned long long now = globaltimer_ns(), last = vq->last_read;
+                if (now - last > kRefreshNs && atomicCAS(&q->last_read, last, now) == last) {
+                    if (ctl->stop) atomicExch(&q->stop, 1ull);
+                    atomicMax(&q->tail, (unsigned long long)ctl->tail);
+                    continue;
+                }
+                // bounded: once no warp has claimed a task for max_idle_ns every
+                // warp leaves, and the poll cap bounds the wait on its own
+                const unsigned long long act = max(idle0, vq->last_active);
+                if ((now > act && now - act > max_idle_ns) || polls >= kMaxPolls) break;
+                __nanosleep(1000);
             }
         }
         t = __shfl_sync(0xffffffffu, t, 0);
@@ -387,7 +418,7 @@ struct dock_server {
     ServeTask *d_tasks = nullptr;
     ServeCtl *d_ctl = nullptr;
     long long *d_done = nullptr;
-    unsigned long long *head = nullptr;
+    ServeDev *q = nullptr;
     float *scratch = nullptr, *best_geno = nullptr, *best_E32 = nullptr;
     double *best_E = nullptr;
     unsigned long long *evals = nullptr;
@@ -446,17 +477,17 @@ int server_create(dock_ctx *ctx, int capacity, int max_atoms, int pop_max, dock_
     }
     memset(S->ctl, 0, sizeof(ServeCtl));
     memset(S->done, 0, sizeof(long long) * capacity);
-    S->head = (unsigned long long *)dev_alloc(ctx, 8, S->stream);
+    S->q = (ServeDev *)dev_alloc(ctx, sizeof(ServeDev), S->stream);
     S->scratch = (float *)dev_alloc(ctx, S->floats_per_warp * 4 * S->warps, S->stream);
     S->best_geno = (float *)dev_alloc(ctx, (size_t)capacity * gmax * 4, S->stream);
     S->best_E32 = (float *)dev_alloc(ctx, (size_t)capacity * 4, S->stream);
     S->best_E = (double *)dev_alloc(ctx, (size_t)capacity * 8, S->stream);
     S->evals = (unsigned long long *)dev_alloc(ctx, (size_t)capacity * 8, S->stream);
-    if (!S->head || !S->scratch || !S->best_geno || !S->best_E32 || !S->best_E || !S->evals) {
+    if (!S->q || !S->scratch || !S->best_geno || !S->best_E32 || !S->best_E || !S->evals) {
         server_destroy(S);
         return set_err(ctx, DOCK_ERR_OOM, "server_create device buffers");
     }
-    e = cudaMemsetAsync(S->head, 0, 8, S->stream);
+    e = cudaMemsetAsync(S->q, 0, sizeof(ServeDev), S->stream);
     if (!e) e = cudaStreamSynchronize(S->stream);
     if (e) {
         server_destroy(S);
@@ -470,9 +501,9 @@ int server_create(dock_ctx *ctx, int capacity, int max_atoms, int pop_max, dock_
 static int server_kick(dock_server *S) {
     if (S->launched && cudaEventQuery(S->running) == cudaErrorNotReady) return DOCK_OK;
     cudaGetLastError();
-    const long long max_idle = 50000;  // x 20 us: an idle warp leaves after about a second
+    const unsigned long long max_idle = 1000000000ull;  // the kernel ends after a second without claims
     lga_serve<<<S->blocks, 32 * S->wpb, S->smem, S->stream>>>(
-        S->d_tasks, S->d_ctl, S->capacity, S->head, S->scratch, S->floats_per_warp, S->pop_max, S->smem_per_warp,
+        S->d_tasks, S->d_ctl, S->capacity, S->q, S->scratch, S->floats_per_warp, S->pop_max, S->smem_per_warp,
         S->best_geno, S->best_E32, S->best_E, S->evals, S->d_done, max_idle);
     ++S->ctx->launches;
     cudaError_t e = cudaGetLastError();
@@ -574,9 +605,9 @@ int server_destroy(dock_server *S) {
     if (!S) return DOCK_ERR_INVALID;
     if (S->ctl) *(volatile int *)&S->ctl->stop = 1;
     __atomic_thread_fence(__ATOMIC_SEQ_CST);
-    if (S->stream) cudaStreamSynchronize(S->stream);  // warps leave at their next claim
+    if (S->stream) cudaStreamSynchronize(S->stream);  // idle warps see stop within a refresh
     dock_ctx *ctx = S->ctx;
-    dev_free(ctx, S->head, S->stream);
+    dev_free(ctx, S->q, S->stream);
     dev_free(ctx, S->scratch, S->stream);
     dev_free(ctx, S->best_geno, S->stream);
     dev_free(ctx, S->best_E32, S->stream);

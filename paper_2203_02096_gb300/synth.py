@@ -26,7 +26,9 @@ TYPE_NAMES = ("C", "A", "N", "NA", "OA", "SA", "HD")
 TYPE_CODE = {name: i for i, name in enumerate(TYPE_NAMES)}
 
 BOND_LENGTH = 1.5        # A, every synthetic bond
-MIN_NONBONDED = 1.2      # A, rejection distance for a newly placed atom
+MIN_13 = 2.2             # A, least distance of atoms 2 or 3 bonds apart
+MIN_15 = 3.6             # A, least distance of atoms 4 or more bonds apart
+PLACE_TRIES = 400        # random directions tried per new atom
 MAX_VALENCE = 4
 GRID_SPACING = 0.375     # A
 POCKET_CENTER = (12.5, -3.25, 7.0)   # deliberately off the origin
@@ -89,27 +91,37 @@ def _unit(rng):
 
 def make_ligand(n_atoms: int, n_torsions: int, type_names=TYPE_NAMES, seed: int = 0) -> Ligand:
     """Random tree ligand: atom k bonds to a uniformly chosen earlier atom of
-    valence < 4, 1.5 A away in a random direction (resampled up to 100 times
-    while it lands within 1.2 A of another atom).  ``n_torsions`` rotatable
-    bonds are drawn among bonds whose two ends both have degree >= 2; when
-    fewer exist, all of them are used (read the effective count from
-    ``Ligand.n_torsions``)."""
+    valence < 4, 1.5 A away in a random direction.  The direction is redrawn
+    (up to PLACE_TRIES times, keeping the least crowded one) while the new
+    atom lands within MIN_13 of an atom 2 or 3 bonds away or within MIN_15 of
+    one 4 or more bonds away, so that the reference conformation has no
+    steric clash of the kind the intramolecular term penalises.
+    ``n_torsions`` rotatable bonds are drawn among bonds whose two ends both
+    have degree >= 2; when fewer exist, all of them are used (read the
+    effective count from ``Ligand.n_torsions``)."""
     if n_atoms < 1:
         raise ValueError("n_atoms must be >= 1")
     rng = np.random.default_rng(seed)
     xyz = np.zeros((n_atoms, 3))
     deg = np.zeros(n_atoms, dtype=np.int64)
+    hops = np.zeros((n_atoms, n_atoms), dtype=np.int64)  # bonds between atoms
     bonds = []
     for k in range(1, n_atoms):
         cand = np.nonzero(deg[:k] < MAX_VALENCE)[0]
         parent = int(cand[rng.integers(len(cand))])
-        p = xyz[parent] + BOND_LENGTH * _unit(rng)
-        for _ in range(100):
-            d = np.linalg.norm(xyz[:k] - p, axis=1)
-            if np.all(d >= MIN_NONBONDED - 1e-9):
-                break
+        hk = hops[parent, :k] + 1
+        need = np.where(hk <= 1, 0.0, np.where(hk <= 3, MIN_13, MIN_15))
+        best, best_slack = None, -np.inf
+        for _ in range(PLACE_TRIES):
             p = xyz[parent] + BOND_LENGTH * _unit(rng)
-        xyz[k] = p
+            slack = float(np.min(np.linalg.norm(xyz[:k] - p, axis=1) - need))
+            if slack > best_slack:
+                best, best_slack = p, slack
+            if slack >= 0.0:
+                break
+        xyz[k] = best
+        hops[k, :k] = hk
+        hops[:k, k] = hk
         bonds.append((parent, k))
         deg[parent] += 1
         deg[k] += 1
