@@ -166,8 +166,10 @@ __device__ __forceinline__ float pair_energy(float r2, float4 c, float &s) {
     const float inv_den = __fdividef(1.f, fmaf(kDielK, ex, 1.f));
     const float eps = fmaf(kDielB, inv_den, kDielA);
     const float inv_eps = __fdividef(1.f, eps);
-    const float eel = c.z * rinv * inv_eps;
-    const float eds = c.w * __expf(-r2e * kHalfInvSig2);
+    // products rounded on their own (never fused into the sum below), so the
+    // energy has the same bits with and without the gradient
+    const float eel = __fmul_rn(__fmul_rn(c.z, rinv), inv_eps);
+    const float eds = __fmul_rn(c.w, __expf(-r2e * kHalfInvSig2));
     if (GRAD) {
         const float dv = fmaf(-12.f * c.x, ri12, (hb ? 10.f : 6.f) * cn * rk) * rinv;
         // eps' / eps with eps' = B k lambda B e / (1 + k e)^2
@@ -176,7 +178,7 @@ __device__ __forceinline__ float pair_energy(float r2, float4 c, float &s) {
         const float dds = -eds * r * kInvSig2;
         s = r2 >= kFloor2 ? (dv + del + dds) * rinv : 0.f;
     }
-    return ev + eel + eds;
+    return __fadd_rn(__fadd_rn(ev, eel), eds);
 }
 
 __device__ __forceinline__ float warp_sum(float v) {

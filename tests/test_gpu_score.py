@@ -52,7 +52,9 @@ def _compare(gpu, system, genos, check_grad=True, require_plain=0.97):
         gerr = np.abs(g - Go).max(axis=1)
         gbad = np.nonzero(smooth & (gerr > grad_tol(Go)))[0]
         assert len(gbad) == 0, [(int(b), float(gerr[b]), float(grad_tol(Go)[b])) for b in gbad[:5]]
-        assert smooth.mean() > 0.5  # near-face / near-cutoff genotypes are excluded, more of them for big ligands
+        # near-face / near-cutoff genotypes are excluded, more of them for big
+        # ligands; enough smooth ones must remain for the check to mean something
+        assert smooth.sum() >= max(8, len(genos) // 4), int(smooth.sum())
     return E, Eo
 
 
