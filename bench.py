@@ -316,7 +316,8 @@ def run(args):
                            ls_threads=args.ls_threads or "auto"),
             "ligands_per_hour": ligands_per_hour,
             "roofline": {"bound": "alu", "kernel": "dock_ls (ADADELTA local search)", "achieved": achieved,
-                         "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                         "traffic": LS_TRAFFIC_BYTES if sources_digest() == LS_TRAFFIC_SOURCES else None,
                          "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 FLOP x 2070 MHz (recipe unit counts, "
                                         "max SM clock of measured)",
                          "flops_per_eval": f_eval, "evals_per_launch": evals_per_ls_launch,
@@ -516,6 +517,26 @@ def pair_list(lig):
                     q.append(b)
         out += [(s, t) for t in range(s + 1, n) if frag[s] != frag[t] and dist[t] >= 4]
     return np.asarray(out, dtype=int).reshape(-1, 2)
+
+
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one ls_kernel
+# launch on the drug-size workload, from one ncu capture (cold caches), and a
+# digest of the kernel sources and input generator it was taken on: the figure
+# is reported only while they are unchanged.
+LS_TRAFFIC_BYTES = 36.61e6
+LS_TRAFFIC_SOURCES = "b10effcf20de9e11"
+
+
+def sources_digest() -> str:
+    import glob
+    import hashlib
+    pkg = os.path.join(ROOT, "paper_2203_02096_gb300")
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(pkg, "csrc", "*"))) + [os.path.join(pkg, "synth.py")]:
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def peak_fp32_tflops() -> float:
