@@ -44,10 +44,31 @@ class Grid(C.Structure):
                 ("map_of_type", C.c_int * 8), ("emap", C.c_int), ("dmap", C.c_int)]
 
 
+class SwParams(C.Structure):
+    _fields_ = [("rho0", C.c_float), ("rho_lo", C.c_float), ("expand", C.c_float), ("contract", C.c_float),
+                ("n_succ", C.c_int), ("n_fail", C.c_int),
+                ("step_t", C.c_float), ("step_q", C.c_float), ("step_tau", C.c_float)]
+
+
+# Solis-Wets constants (readings): rho from 1 down to 0.01, x2 after 4
+# successes, x0.5 after 4 failures; half-widths 1 A, 0.2, 0.75 rad at rho = 1.
+SW_DEFAULTS = dict(rho0=1.0, rho_lo=0.01, expand=2.0, contract=0.5, n_succ=4, n_fail=4,
+                   step_t=1.0, step_q=0.2, step_tau=0.75)
+
+
+def make_sw(**kw) -> SwParams:
+    v = dict(SW_DEFAULTS, **kw)
+    s = SwParams()
+    for k, x in v.items():
+        setattr(s, k, x)
+    return s
+
+
 class Params(C.Structure):
     _fields_ = [("pop_size", C.c_int), ("nruns", C.c_int), ("max_evals", C.c_longlong),
                 ("ls_count", C.c_int), ("ls_iters", C.c_int), ("rho", C.c_double), ("eps", C.c_double),
-                ("p_tour", C.c_float), ("p_cross", C.c_float), ("p_mut", C.c_float), ("trans_mut", C.c_float)]
+                ("p_tour", C.c_float), ("p_cross", C.c_float), ("p_mut", C.c_float), ("trans_mut", C.c_float),
+                ("ls_method", C.c_int), ("sw", SwParams)]
 
 
 def _L():
@@ -86,6 +107,8 @@ def _L():
             "orc_ls_picks": (None, [i, i, u64, u32, u32, vp]),
             "orc_adadelta_step": (None, [i, i, d, d, vp, vp, vp, vp]),
             "orc_local_search": (d, [vp, P(Grid), vp, i, d, d, vp, vp]),
+            "orc_solis_wets": (d, [vp, P(Grid), vp, d, i, P(SwParams), u64, u32, u32, u32, vp, P(C.c_longlong),
+                                   vp, P(i)]),
             "orc_dock": (i, [vp, P(Grid), P(Params), u64, i, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
@@ -311,8 +334,11 @@ def philox(ctr, key):
 
 
 def make_params(pop_size=150, nruns=1, max_evals=10_000, ls_rate_pct=6, ls_iters=100, rho=0.8, eps=1e-2,
-                p_tour=0.6, p_cross=0.8, p_mut=0.02, trans_mut=2.0, ls_count=None) -> Params:
+                p_tour=0.6, p_cross=0.8, p_mut=0.02, trans_mut=2.0, ls_count=None, ls_method=0,
+                sw: SwParams | None = None) -> Params:
     p = Params()
+    p.ls_method = ls_method
+    p.sw = sw if sw is not None else make_sw()
     p.pop_size, p.nruns, p.max_evals = pop_size, nruns, max_evals
     p.ls_count = (ls_rate_pct * pop_size + 99) // 100 if ls_count is None else ls_count
     p.ls_iters, p.rho, p.eps = ls_iters, rho, eps
@@ -355,6 +381,21 @@ def local_search(lig: OracleLigand, grid, x0, iters, rho=0.8, eps=1e-2):
     trace = np.zeros(max(iters, 1))
     e = _L().orc_local_search(lig.h, grid.ref, _p(x0), int(iters), float(rho), float(eps), _p(out), _p(trace))
     return e, out, trace[:iters]
+
+
+def solis_wets(lig: OracleLigand, grid, x0, iters, E0=None, sw: SwParams | None = None, seed=0, run=0, gen=0,
+               entity=0):
+    """One Solis-Wets search from x0 (its energy E0, or None to evaluate it).
+    Returns (E, x, evals, iterations done, trace [iters_done, 4])."""
+    x0 = _f32(x0)
+    out = np.zeros_like(x0)
+    trace = np.full((max(iters, 1), 4), np.nan)
+    n = C.c_longlong(0)
+    it = C.c_int(0)
+    e = _L().orc_solis_wets(lig.h, grid.ref, _p(x0), float("nan") if E0 is None else float(E0), int(iters),
+                            C.byref(sw if sw is not None else make_sw()), int(seed), int(run), int(gen),
+                            int(entity), _p(out), C.byref(n), _p(trace), C.byref(it))
+    return e, out, int(n.value), int(it.value), trace[:it.value]
 
 
 def dock(lig: OracleLigand, grid, params: Params, seed: int, nthreads=None):

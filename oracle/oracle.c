@@ -18,7 +18,9 @@
  * every form and constant below is a reading fixed by this project and listed
  * as such in the design notes.  The local search is ADADELTA (Zeiler 2012),
  * which the paper reaches only through its citation of gradient-based local
- * search in AutoDock-GPU; the paper's own miniapp uses Solis-Wets.
+ * search in AutoDock-GPU; the paper's own miniapp uses Solis-Wets, which
+ * orc_solis_wets restates (Solis and Wets 1981, adaptive step with a bias
+ * term) as the second local-search method.
  *
  * Precision: energies, forces, poses, gradients and ADADELTA in FP64.  The
  * genetic operators act on FP32 genes with explicitly rounded FP32 operations
@@ -707,7 +709,7 @@ void orc_philox(const uint32_t *ctr, const uint32_t *key, uint32_t *out) {
 
 /* Stream layout of the search: counter = (purpose << 16 | draw, entity,
  * generation, run), key = (seed low word, seed high word). */
-enum { P_INIT = 1, P_SELECT = 2, P_CROSS = 3, P_MUTATE = 4, P_LSPICK = 5 };
+enum { P_INIT = 1, P_SELECT = 2, P_CROSS = 3, P_MUTATE = 4, P_LSPICK = 5, P_SW = 6 };
 
 static void draw4(uint64_t seed, uint32_t run, uint32_t gen, uint32_t entity, uint32_t purpose, uint32_t draw,
                   uint32_t *w) {
@@ -726,14 +728,27 @@ static uint32_t uidx(uint32_t w, uint32_t n) { return (uint32_t)(((uint64_t)(w >
 /* rates and operator forms are this project's readings).  FP32 genes, every  */
 /* arithmetic step one rounded IEEE single operation in a fixed order.        */
 
+/* Solis-Wets constants (this project's readings): initial and lowest step
+ * scale, expansion and contraction factors, the runs of consecutive
+ * successes / failures that trigger them, and the deviation half-width per
+ * gene block at scale 1 (translation in A, quaternion component, torsion in
+ * radians). */
+typedef struct {
+    float rho0, rho_lo, expand, contract;
+    int n_succ, n_fail;
+    float step_t, step_q, step_tau;
+} orc_sw_t;
+
 typedef struct {
     int pop_size;
     int nruns;
     long long max_evals;
     int ls_count;   /* individuals given a local search per generation */
-    int ls_iters;   /* ADADELTA iterations per local search            */
+    int ls_iters;   /* iterations per local search (ADADELTA or Solis-Wets) */
     double rho, eps;
     float p_tour, p_cross, p_mut, trans_mut;
+    int ls_method;  /* 0 = ADADELTA, 1 = Solis-Wets */
+    orc_sw_t sw;
 } orc_params;
 
 static const float PI_F = 3.14159265358979323846f;
@@ -921,11 +936,106 @@ double orc_local_search(const orc_lig *L, const orc_grid *g, const float *x0, in
 }
 
 /* ------------------------------------------------------------------------ */
+/* Solis-Wets local search (Solis and Wets 1981, the adaptive random search   */
+/* with a bias term), the memetic step of the paper's miniapp (Section II-A). */
+/* State: the current point x (always the best seen), its energy, a bias b    */
+/* (start 0), a step scale rho (start rho0) and the runs of consecutive       */
+/* successes and failures.  One iteration draws a deviation                   */
+/*     xi_j = b_j + rho * step(block of j) * u_j,   u_j uniform in [-1, 1)     */
+/* and tries x + xi; if that is not lower it tries x - xi.  A success moves   */
+/* x there and sets b <- 0.2 b + 0.4 xi (forward) or b <- b - 0.4 xi          */
+/* (backward); a failure halves b.  n_succ successes in a row multiply rho    */
+/* by expand, n_fail failures in a row by contract (either resets both runs). */
+/* The search ends after iters iterations or once rho < rho_lo.  Genes, xi,   */
+/* b and rho are FP32, each step one rounded single operation, so that given  */
+/* the same accept decisions the GPU reproduces every point bit for bit;      */
+/* energies are FP64.  u_j is word j mod 4 of the Philox block              */
+/* (P_SW << 16 | 10 it + j / 4, entity, gen, run).                              */
+
+static double score_f(const orc_lig *L, const orc_grid *g, const float *ge);
+
+/* torsion wrap to [-pi, pi) for any finite x, FP32 single operations */
+static float wrap_any_f(float x) {
+    float k = floorf((x + PI_F) / TWO_PI_F);
+    return x - TWO_PI_F * k;
+}
+
+static float sw_step_of(const orc_sw_t *S, int j) {
+    return j < 3 ? S->step_t : (j < 7 ? S->step_q : S->step_tau);
+}
+
+/* E0: energy of x0 (NaN: evaluated here, one evaluation).  trace (optional,
+ * [iters][4]): energy of x + xi, of x - xi (NaN if not tried), rho used and
+ * the outcome (+1 forward success, -1 backward success, 0 failure); rows
+ * after the last iteration are left untouched.  Returns the final energy;
+ * x_out = final point, quaternion normalised; *evals = energies computed. */
+double orc_solis_wets(const orc_lig *L, const orc_grid *g, const float *x0, double E0, int iters,
+                      const orc_sw_t *S, uint64_t seed, uint32_t run, uint32_t gen, uint32_t entity,
+                      float *x_out, long long *evals, double *trace, int *iters_done) {
+    const int G = 7 + L->nt;
+    float x[7 + ORC_MAX_TORS], b[7 + ORC_MAX_TORS], xi[7 + ORC_MAX_TORS], y[7 + ORC_MAX_TORS];
+    long long n = 0;
+    for (int j = 0; j < G; ++j) { x[j] = x0[j]; b[j] = 0.0f; }
+    double E = E0;
+    if (isnan(E)) { E = score_f(L, g, x); ++n; }
+    float rho = S->rho0;
+    int ns = 0, nf = 0, it = 0;
+    for (; it < iters && rho >= S->rho_lo; ++it) {
+        uint32_t w[4];
+        for (int j = 0; j < G; ++j) {
+            if ((j & 3) == 0) draw4(seed, run, gen, entity, P_SW, (uint32_t)(10 * it + j / 4), w);
+            float u = 2.0f * unif(w[j & 3]) - 1.0f;
+            xi[j] = b[j] + (rho * sw_step_of(S, j)) * u;
+        }
+        for (int j = 0; j < G; ++j) y[j] = x[j] + xi[j];
+        for (int k = 7; k < G; ++k) y[k] = wrap_any_f(y[k]);
+        double Ef = score_f(L, g, y), Eb = NAN;
+        ++n;
+        int outcome = 0;
+        if (Ef < E) {
+            memcpy(x, y, sizeof(float) * G);
+            E = Ef;
+            for (int j = 0; j < G; ++j) b[j] = 0.2f * b[j] + 0.4f * xi[j];
+            outcome = 1;
+        } else {
+            for (int j = 0; j < G; ++j) y[j] = x[j] - xi[j];
+            for (int k = 7; k < G; ++k) y[k] = wrap_any_f(y[k]);
+            Eb = score_f(L, g, y);
+            ++n;
+            if (Eb < E) {
+                memcpy(x, y, sizeof(float) * G);
+                E = Eb;
+                for (int j = 0; j < G; ++j) b[j] = b[j] - 0.4f * xi[j];
+                outcome = -1;
+            } else {
+                for (int j = 0; j < G; ++j) b[j] = 0.5f * b[j];
+            }
+        }
+        if (trace) {
+            trace[4 * it] = Ef;
+            trace[4 * it + 1] = Eb;
+            trace[4 * it + 2] = rho;
+            trace[4 * it + 3] = outcome;
+        }
+        if (outcome) { ++ns; nf = 0; } else { ++nf; ns = 0; }
+        if (ns >= S->n_succ) { rho = rho * S->expand; ns = 0; }
+        else if (nf >= S->n_fail) { rho = rho * S->contract; nf = 0; }
+    }
+    memcpy(x_out, x, sizeof(float) * G);
+    normalise_q(x_out);
+    if (evals) *evals = n;
+    if (iters_done) *iters_done = it;
+    return E;
+}
+
+/* ------------------------------------------------------------------------ */
 /* The Lamarckian GA over independent runs (Section II-A).  Per generation:   */
 /* children (elitism, tournaments, crossover, mutation) and their energies;   */
-/* ADADELTA on ls_count individuals drawn without replacement, written back;  */
-/* evaluation count += (pop-1) + ls_count*ls_iters (the per-run sum of         */
-/* Listing 1).  Stops at the first generation boundary with evals >= max.    */
+/* a local search (ADADELTA or Solis-Wets) on ls_count individuals drawn     */
+/* without replacement, written back; evaluation count += (pop-1) + the       */
+/* energies the local searches computed (the per-run sum of Listing 1:        */
+/* ls_count*ls_iters for ADADELTA).  Stops at the first generation boundary   */
+/* with evals >= max_evals.                                                   */
 
 typedef struct {
     const orc_lig *L;
@@ -963,11 +1073,20 @@ static void run_lga(run_job_t *J) {
         EB[0] = EA[elite];
         for (int s = 1; s < pop; ++s) EB[s] = score_f(L, J->g, B + (size_t)s * G);
         orc_ls_picks(pop, P->ls_count, J->seed, (uint32_t)J->run, gen, picks);
+        long long ls_evals = 0;
         for (int k = 0; k < P->ls_count; ++k) {
             float *ind = B + (size_t)picks[k] * G;
-            EB[picks[k]] = orc_local_search(L, J->g, ind, P->ls_iters, P->rho, P->eps, ind, NULL);
+            if (P->ls_method == 1) {
+                long long n = 0;
+                EB[picks[k]] = orc_solis_wets(L, J->g, ind, EB[picks[k]], P->ls_iters, &P->sw, J->seed,
+                                              (uint32_t)J->run, gen, (uint32_t)k, ind, &n, NULL, NULL);
+                ls_evals += n;
+            } else {
+                EB[picks[k]] = orc_local_search(L, J->g, ind, P->ls_iters, P->rho, P->eps, ind, NULL);
+                ls_evals += P->ls_iters;
+            }
         }
-        evals += (pop - 1) + (long long)P->ls_count * P->ls_iters;
+        evals += (pop - 1) + ls_evals;
         float *t = A; A = B; B = t;
         double *te = EA; EA = EB; EB = te;
     }
@@ -1004,6 +1123,7 @@ static void *run_worker(void *arg) {
 int orc_dock(const orc_lig *L, const orc_grid *g, const orc_params *P, uint64_t seed, int nthreads,
              float *best_geno, double *best_E, long long *evals) {
     if (P->pop_size < 2 || P->ls_count < 0 || P->ls_count > P->pop_size || P->nruns < 1) return ORC_EINVAL;
+    if (P->ls_method == 1 && P->ls_iters > 6553) return ORC_EINVAL;  /* 10 it + 9 must fit 16 bits */
     int G = 7 + L->nt;
     run_job_t *jobs = (run_job_t *)malloc(sizeof(run_job_t) * P->nruns);
     for (int r = 0; r < P->nruns; ++r) {
