@@ -301,6 +301,7 @@ def run(args):
     batch = score_grad_throughput(ctx, G, w.box, dev) if not args.no_batch else None
     multi = batched_docking(ctx, dev) if not args.no_batch else None
     serving = serving_sweep(ctx, dev) if not args.no_batch else None
+    solis = solis_wets_vs_adadelta(ctx, G, L, w, dev, out, value) if not args.no_batch else None
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -332,6 +333,7 @@ def run(args):
             "score_grad_batch": batch,
             "batched_docking": multi,
             "serving": serving,
+            "solis_wets": solis,
             "best_energy_median": float(np.median(out["best_E"].cpu().numpy())),
         }
         print(json.dumps(line), flush=True)
@@ -482,6 +484,35 @@ def serving_sweep(ctx, dev, rates=(10, 30, 100, 300, 1000), seconds: float = 2.0
             "sweep": out,
             "plain": {"requests_per_s": n_plain / t_plain, "ligands_per_hour": 3600.0 * n_plain / t_plain,
                       "latency_s_median": float(np.median(lat))}}
+
+
+def solis_wets_vs_adadelta(ctx, G, L, w, dev, ada_out, ada_value):
+    """The paper's own local search (Solis-Wets, energies only) against
+    ADADELTA (score+gradient) on the same drug-size docking at the same
+    evaluation budget: evaluations/s and the best energies reached (FP64
+    re-scores of each run's best pose), one timed docking after one warm-up."""
+    import torch
+
+    from paper_2203_02096_gb300 import capi
+    P = capi.default_params(pop_size=w.pop_size, nruns=w.nruns, max_evals=w.max_evals, ls_iters=w.ls_iters,
+                            ls_method=1)
+    stream = torch.cuda.current_stream(dev)
+    out = capi.dock_async(ctx, G, L, P, w.seed + 7)
+    torch.cuda.synchronize(dev)
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    out = capi.dock_async(ctx, G, L, P, w.seed + 8, out=out)
+    t1.record(stream)
+    torch.cuda.synchronize(dev)
+    s = t0.elapsed_time(t1) / 1e3
+    sw_E = out["best_E"].cpu().numpy()
+    ada_E = ada_out["best_E"].cpu().numpy()
+    return {"workload": "drug-size ligand, 50 runs x 2.5M evaluations, pop 150, local search on 6% "
+                        "(ADADELTA 300 iterations / Solis-Wets at most 300 iterations)",
+            "solis_wets_evals_per_s": float(out["evals"].sum().item()) / s, "solis_wets_seconds": s,
+            "adadelta_evals_per_s": ada_value,
+            "best_E_median": {"solis_wets": float(np.median(sw_E)), "adadelta": float(np.median(ada_E))},
+            "best_E_min": {"solis_wets": float(sw_E.min()), "adadelta": float(ada_E.min())}}
 
 
 def pair_list(lig):

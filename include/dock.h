@@ -70,13 +70,20 @@ typedef struct {
 
 /* Search parameters (paper, Section II-A: population 150, crossover,
  * fitness-based selection, local search on a random sample of each
- * generation; the rates and the ADADELTA constants are this library's). */
+ * generation; the rates and the ADADELTA and Solis-Wets constants are this
+ * library's).  Local search: ADADELTA (default; one score+gradient per
+ * iteration, ls_iters iterations) or Solis-Wets (the paper's miniapp search,
+ * Solis and Wets 1981: adaptive random steps with a bias term, energies
+ * only, one or two per iteration, at most ls_iters <= 6553 iterations, ends
+ * early once the step scale falls below sw_rho_lo).  Evaluations are
+ * counted as computed; a run stops at the first generation boundary where
+ * its count reaches max_evals. */
 typedef struct {
     int pop_size;      /* individuals per run (>= 2), default 150                  */
     int nruns;         /* independent runs, default 10                              */
     int64_t max_evals; /* per-run evaluation budget, default 100000                 */
     int ls_count;      /* local searches per generation; default ceil(6% pop_size)  */
-    int ls_iters;      /* ADADELTA iterations per local search, default 100         */
+    int ls_iters;      /* iterations per local search, default 100                  */
     float rho, eps;    /* ADADELTA decay and conditioner, default 0.8, 1e-2         */
     float p_tour;      /* probability the fitter of two wins a tournament, 0.6      */
     float p_cross;     /* two-point crossover probability, 0.8                      */
@@ -85,6 +92,14 @@ typedef struct {
     int ls_threads;    /* threads evaluating one local-search chain: 32, 64, 128,
                           256, or 0 = chosen from the chain count (the paper's
                           threads-per-block knob, Section V-B); default 0       */
+    int ls_method;     /* 0 = ADADELTA (default), 1 = Solis-Wets                    */
+    float sw_rho0;     /* Solis-Wets step scale at the start, default 1.0           */
+    float sw_rho_lo;   /* ... the search ends once it is below this, default 0.01   */
+    float sw_expand;   /* scale factor after sw_succ successes in a row, 2.0        */
+    float sw_contract; /* scale factor after sw_fail failures in a row, 0.5         */
+    int sw_succ, sw_fail; /* default 4, 4                                          */
+    float sw_step[3];  /* deviation half-widths at scale 1: translation (A) 1.0,
+                          quaternion component 0.2, torsion (rad) 0.75             */
 } dock_params;
 
 /* Library version (major*10000 + minor*100 + patch). */
@@ -164,15 +179,19 @@ int pose_batch(dock_ctx *ctx, const dock_ligand *lig, const float *geno, int B, 
  * Runs params->nruns independent searches of params->pop_size individuals
  * until each has spent params->max_evals evaluations (checked at generation
  * boundaries).  Per generation: elitism, tournament selection, two-point
- * crossover, mutation, evaluation of the new individuals; ADADELTA on
- * ls_count individuals drawn without replacement, best point written back;
- * the per-run evaluation count grows by (pop_size-1) + ls_count*ls_iters.
- * Random numbers: Philox4x32-10 keyed by seed, counter (purpose<<16|draw,
- * individual, generation, run).  Deterministic for a given seed.
- * dock(): host outputs best_geno [nruns][G] (unit quaternion), best_E
- * [nruns] (FP64 re-score of best_geno), evals_used [nruns]; blocks until
- * done.  dock_async(): the same into device buffers (best_E32: the FP32
- * energy the search kept), queued on `stream`. */
+ * crossover, mutation, evaluation of the new individuals; the local search
+ * (ADADELTA or Solis-Wets) on ls_count individuals drawn without
+ * replacement, result written back; the per-run evaluation count grows by
+ * (pop_size-1) + the local searches' evaluations (ls_count*ls_iters for
+ * ADADELTA).  Random numbers: Philox4x32-10 keyed by seed, counter
+ * (purpose<<16|draw, individual, generation, run).  Deterministic for a
+ * given seed.  dock(): host outputs best_geno [nruns][G] (unit quaternion),
+ * best_E [nruns] (FP64 re-score of best_geno), evals_used [nruns]; blocks
+ * until done.  dock_async(): the same into device buffers (best_E32: the
+ * FP32 energy the search kept), queued on `stream`; with Solis-Wets, whose
+ * evaluation count is known only on the device, it also reads the runs'
+ * counters back a few times (a stream synchronisation each) to decide how
+ * many more generations to queue. */
 int dock(dock_ctx *ctx, const dock_grids *grids, const dock_ligand *lig, const dock_params *params, uint64_t seed,
          float *best_geno, double *best_E, int64_t *evals_used);
 int dock_async(dock_ctx *ctx, const dock_grids *grids, const dock_ligand *lig, const dock_params *params,
@@ -248,6 +267,8 @@ int server_destroy(dock_server *srv);
  *    (the counters are cleared at the start of each call): calls that
  *    overlap on the GPU -- on different streams, or from different host
  *    threads -- race on it; serialise them.
+ *  - It runs the ADADELTA local search only: ls_method != 0 fails with
+ *    DOCK_ERR_INVALID.
  * Outputs and arguments as dock_async. */
 #define DOCK_NOALLOC_SCRATCH_BYTES (8u << 20)
 int dock_async_noalloc(dock_ctx *ctx, const dock_grids *grids, const dock_ligand *lig, const dock_params *params,
@@ -278,6 +299,17 @@ int dock_local_search(dock_ctx *ctx, const dock_grids *grids, const dock_ligand 
                       int iters, float rho, float eps, int threads, float *x_best, float *E_best, void *stream);
 int dock_philox(dock_ctx *ctx, const uint32_t *ctr, int n, uint32_t key_lo, uint32_t key_hi, uint32_t *out,
                 void *stream);
+/* dock_solis_wets: the Solis-Wets local search (paper, Section II-A; Solis
+ * and Wets 1981) from B start points x0 [B][G] (device), with their energies
+ * E0 [B] (device; NULL = evaluate each start first, one more evaluation),
+ * params->ls_iters iterations at most, the sw_* constants and ls_threads of
+ * params.  Chain c draws its deviates from the Philox blocks
+ * (6 << 16 | 10 it + j / 4, c, generation, run) under key = seed.  Outputs
+ * (device): x_best [B][G] (quaternion normalised), E_best [B], evals [B]
+ * (energies computed; may be NULL).  Errors: ls_iters > 6553. */
+int dock_solis_wets(dock_ctx *ctx, const dock_grids *grids, const dock_ligand *lig, const float *x0,
+                    const float *E0, int B, const dock_params *params, uint64_t seed, uint32_t run,
+                    uint32_t generation, float *x_best, float *E_best, int64_t *evals, void *stream);
 
 /* ---- tracing ----
  * With timing on, every kernel launch of dock/dock_async/score_* is

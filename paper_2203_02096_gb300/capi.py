@@ -36,7 +36,8 @@ _P = C.POINTER
 class DockParams(C.Structure):
     _fields_ = [("pop_size", _i), ("nruns", _i), ("max_evals", _i64), ("ls_count", _i), ("ls_iters", _i),
                 ("rho", _f), ("eps", _f), ("p_tour", _f), ("p_cross", _f), ("p_mut", _f), ("trans_mut", _f),
-                ("ls_threads", _i)]
+                ("ls_threads", _i), ("ls_method", _i), ("sw_rho0", _f), ("sw_rho_lo", _f), ("sw_expand", _f),
+                ("sw_contract", _f), ("sw_succ", _i), ("sw_fail", _i), ("sw_step", _f * 3)]
 
 
 ALLOC_FN = C.CFUNCTYPE(_vp, _sz, _vp, _vp)
@@ -78,6 +79,7 @@ SIGNATURES = {
     "dock_ls_picks": (_i, [_vp, _i, _i, _i, _u64, _u32, _vp, _vp]),
     "dock_local_search": (_i, [_vp, _vp, _vp, _vp, _i, _i, _f, _f, _i, _vp, _vp, _vp]),
     "dock_philox": (_i, [_vp, _vp, _i, _u32, _u32, _vp, _vp]),
+    "dock_solis_wets": (_i, [_vp, _vp, _vp, _vp, _vp, _i, _P(DockParams), _u64, _u32, _u32, _vp, _vp, _vp, _vp]),
     "dock_set_timing": (_i, [_vp, _i]),
     "dock_kernel_time": (_i, [_vp, C.c_char_p, _P(_d), _P(_i64)]),
     "dock_reset_timing": (_i, [_vp]),
@@ -132,6 +134,8 @@ def default_params(**kw) -> DockParams:
     p = DockParams()
     load().dock_default_params(C.byref(p))
     for k, v in kw.items():
+        if k == "sw_step":
+            v = (_f * 3)(*v)
         setattr(p, k, v)
     return p
 
@@ -441,6 +445,20 @@ def dock_local_search(ctx, grids, lig, x0: torch.Tensor, iters: int, rho=0.8, ep
     ctx.check(ctx.lib.dock_local_search(ctx.h, grids.h, lig.h, _ptr(x0), B, int(iters), float(rho), float(eps),
                                         int(threads), _ptr(xb), _ptr(Eb), _stream(stream)), "dock_local_search")
     return xb, Eb
+
+
+def dock_solis_wets(ctx, grids, lig, x0: torch.Tensor, params: DockParams, E0: torch.Tensor | None = None,
+                    seed: int = 0, run: int = 0, generation: int = 0, stream=None):
+    """Solis-Wets searches from the rows of x0 (device); returns (x_best,
+    E_best, evals) as device tensors."""
+    B = x0.shape[0]
+    xb = torch.empty_like(x0)
+    Eb = torch.empty(B, dtype=torch.float32, device=x0.device)
+    ev = torch.empty(B, dtype=torch.int64, device=x0.device)
+    ctx.check(ctx.lib.dock_solis_wets(ctx.h, grids.h, lig.h, _ptr(x0), _ptr(E0) if E0 is not None else None, B,
+                                      C.byref(params), int(seed), int(run), int(generation), _ptr(xb), _ptr(Eb),
+                                      _ptr(ev), _stream(stream)), "dock_solis_wets")
+    return xb, Eb, ev
 
 
 def dock_philox(ctx, ctr: torch.Tensor, key_lo: int, key_hi: int, stream=None) -> torch.Tensor:

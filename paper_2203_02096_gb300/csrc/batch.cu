@@ -24,11 +24,39 @@ namespace {
 
 struct BatchConst {
     int pop, n_ls, iters;
-    long long ngen;
+    long long max_evals;
     float rho, eps;
     float p_tour, p_cross, p_mut, trans_mut;
     int gstride;  // genes per output row (DOCK_MAX_TORSIONS + 7)
+    int method;   // 0 = ADADELTA, 1 = Solis-Wets
+    SwConst sw;
 };
+
+BatchConst batch_const(const dock_params &P) {
+    BatchConst BC;
+    BC.pop = P.pop_size;
+    BC.n_ls = P.ls_count;
+    BC.iters = P.ls_iters;
+    BC.max_evals = P.max_evals;
+    BC.rho = P.rho;
+    BC.eps = P.eps;
+    BC.p_tour = P.p_tour;
+    BC.p_cross = P.p_cross;
+    BC.p_mut = P.p_mut;
+    BC.trans_mut = P.trans_mut;
+    BC.gstride = 7 + DOCK_MAX_TORSIONS;
+    BC.method = P.ls_method;
+    BC.sw.rho0 = P.sw_rho0;
+    BC.sw.rho_lo = P.sw_rho_lo;
+    BC.sw.expand = P.sw_expand;
+    BC.sw.contract = P.sw_contract;
+    BC.sw.n_succ = P.sw_succ;
+    BC.sw.n_fail = P.sw_fail;
+    BC.sw.step_t = P.sw_step[0];
+    BC.sw.step_q = P.sw_step[1];
+    BC.sw.step_tau = P.sw_step[2];
+    return BC;
+}
 
 // Scratch of one warp: two populations, their energies and a pop-long
 // index array for the local-search picks.
@@ -48,7 +76,26 @@ __device__ WarpScratch warp_scratch(float *base, size_t floats_per_warp, int gw,
     return S;
 }
 
-// One docking run by one warp.  Returns the per-run evaluation count.
+// The two local searches for one warp, kept out of line: the run loop around
+// them then keeps its own registers instead of spilling them.
+__device__ __noinline__ float sw_chain_warp(const LigandDev &L, const GridDev &G, float *ws, const EvalLayout &Y,
+                                            float *x, float e0, int iters, const SwConst &S, uint2 key, uint32_t run,
+                                            uint32_t gen, uint32_t entity, long long &n) {
+    const dev::Team<1> tm(threadIdx.x & 31);
+    return sw_chain<1>(L, G, ws, Y, tm, x, e0, x, iters, S, key, run, gen, entity, n);
+}
+
+__device__ __noinline__ float ls_chain_warp(const LigandDev &L, const GridDev &G, float *ws, const EvalLayout &Y,
+                                            float *x, int iters, float rho, float eps) {
+    const dev::Team<1> tm(threadIdx.x & 31);
+    return ls_chain<1>(L, G, ws, Y, tm, x, x, iters, rho, eps);
+}
+
+// One docking run by one warp: generations until the run's evaluation count
+// reaches max_evals (each adds >= pop - 1).  Returns the count.  METHOD: the
+// local search compiled in (0 ADADELTA, 1 Solis-Wets, inlined), or -1: the
+// one P.method names, called out of line.
+template <int METHOD>
 __device__ long long dock_run_warp(const LigandDev &L, const GridDev &G, const GaConst &C, const BatchConst &P,
                                    float *ws, const EvalLayout &Yn, const EvalLayout &Yg, WarpScratch S, int run,
                                    float *best_geno, float *best_E) {
@@ -64,7 +111,7 @@ __device__ long long dock_run_warp(const LigandDev &L, const GridDev &G, const G
         __syncwarp();
     }
     long long evals = pop;
-    for (long long gen = 1; gen <= P.ngen; ++gen) {
+    for (long long gen = 1; evals < P.max_evals; ++gen) {
         const uint32_t g32 = (uint32_t)gen;
         float be;
         const int bi = run_argmin(S.EA, pop, lane, be);  // elitism
@@ -90,14 +137,30 @@ __device__ long long dock_run_warp(const LigandDev &L, const GridDev &G, const G
                 S.picks[j] = t;
             }
         __syncwarp();
+        long long ls_evals = 0;
         for (int k = 0; k < P.n_ls && P.iters > 0; ++k) {
             const int ind = S.picks[k];
             float *x = S.B + (size_t)ind * Gn;
-            const float best = ls_chain<1>(L, G, ws, Yg, tm, x, x, P.iters, P.rho, P.eps);
+            float best;
+            if (METHOD == 1 || (METHOD < 0 && P.method == 1)) {
+                long long n = 0;
+                if (METHOD == 1)
+                    best = sw_chain<1>(L, G, ws, Yn, tm, x, S.EB[ind], x, P.iters, P.sw, C.key, (uint32_t)run, g32,
+                                       (uint32_t)k, n);
+                else
+                    best = sw_chain_warp(L, G, ws, Yn, x, S.EB[ind], P.iters, P.sw, C.key, (uint32_t)run, g32,
+                                         (uint32_t)k, n);
+                ls_evals += n;
+            } else {
+                if (METHOD == 0) best = ls_chain<1>(L, G, ws, Yg, tm, x, x, P.iters, P.rho, P.eps);
+                else best = ls_chain_warp(L, G, ws, Yg, x, P.iters, P.rho, P.eps);
+                ls_evals += P.iters;
+            }
+            __syncwarp();
             if (lane == 0) S.EB[ind] = best;
             __syncwarp();
         }
-        evals += (pop - 1) + (long long)P.n_ls * P.iters;
+        evals += (pop - 1) + ls_evals;
         float *t = S.A; S.A = S.B; S.B = t;
         t = S.EA; S.EA = S.EB; S.EB = t;
         __syncwarp();
@@ -122,6 +185,7 @@ struct Task {
     unsigned long long seed;
 };
 
+template <int METHOD>
 __global__ void __launch_bounds__(128, 4)
 lga_persistent(const LigandDev *__restrict__ ligs, GridDev G, const Task *__restrict__ tasks, int n_tasks, int *next,
                BatchConst P, float *scratch, size_t floats_per_warp, int gmax, size_t smem_per_warp,
@@ -149,8 +213,8 @@ lga_persistent(const LigandDev *__restrict__ ligs, GridDev G, const Task *__rest
         C.key = make_uint2((uint32_t)T.seed, (uint32_t)(T.seed >> 32));
         const EvalLayout Yn = eval_layout(L.n_atoms, L.n_frag, L.nb8, false, 1);
         const EvalLayout Yg = eval_layout(L.n_atoms, L.n_frag, L.nb8, true, 1);
-        const long long ev = dock_run_warp(L, G, C, P, ws, Yn, Yg, S, T.run, best_geno + (size_t)T.out * P.gstride,
-                                           best_E32 + T.out);
+        const long long ev = dock_run_warp<METHOD>(L, G, C, P, ws, Yn, Yg, S, T.run,
+                                                   best_geno + (size_t)T.out * P.gstride, best_E32 + T.out);
         if (lane == 0) evals[T.out] = (unsigned long long)ev;
         __syncwarp();
     }
@@ -181,6 +245,7 @@ extern "C" int dock_batch(dock_ctx *ctx, const dock_grids *grids, const dock_lig
     if (P.pop_size < 2 || P.pop_size > 4096 || P.nruns < 1 || P.max_evals < 0 || P.ls_count > P.pop_size ||
         P.ls_count > 256 || P.ls_iters < 0 || !(P.rho >= 0.f && P.rho < 1.f) || !(P.eps > 0.f))
         return set_err(ctx, DOCK_ERR_INVALID, "invalid dock_params");
+    if (int rc0 = check_sw(ctx, P)) return rc0;
     cudaStream_t s = (cudaStream_t)stream;
     size_t smem_per_warp = 0;
     std::vector<LigandDev> hl(n_ligs);
@@ -210,30 +275,19 @@ extern "C" int dock_batch(dock_ctx *ctx, const dock_grids *grids, const dock_lig
     int wpb = 4;
     while (wpb > 1 && smem_per_warp * 4 * wpb > ctx->smem_optin) wpb >>= 1;
     const size_t smem = smem_per_warp * 4 * wpb;
+    auto kern = P.ls_method == 1 ? lga_persistent<1> : lga_persistent<0>;
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(lga_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e) return cuda_err(ctx, e, "dock_batch attributes");
     }
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lga_persistent, 32 * wpb, smem);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * wpb, smem);
     if (e || per_sm < 1) return e ? cuda_err(ctx, e, "dock_batch occupancy") : set_err(ctx, DOCK_ERR_SIZE, "no occupancy");
     int blocks = per_sm * ctx->num_sms;
     blocks = std::min(blocks, (n_tasks + wpb - 1) / wpb);
     const int warps = blocks * wpb;
 
-    BatchConst BC;
-    BC.pop = P.pop_size;
-    BC.n_ls = P.ls_count;
-    BC.iters = P.ls_iters;
-    const long long per_gen = (long long)(P.pop_size - 1) + (long long)P.ls_count * P.ls_iters;
-    BC.ngen = P.max_evals > P.pop_size ? (P.max_evals - P.pop_size + per_gen - 1) / per_gen : 0;
-    BC.rho = P.rho;
-    BC.eps = P.eps;
-    BC.p_tour = P.p_tour;
-    BC.p_cross = P.p_cross;
-    BC.p_mut = P.p_mut;
-    BC.trans_mut = P.trans_mut;
-    BC.gstride = gmax;
+    const BatchConst BC = batch_const(P);
 
     LigandDev *d_ligs = (LigandDev *)dev_alloc(ctx, sizeof(LigandDev) * n_ligs, s);
     Task *d_tasks = (Task *)dev_alloc(ctx, sizeof(Task) * n_tasks, s);
@@ -251,8 +305,8 @@ extern "C" int dock_batch(dock_ctx *ctx, const dock_grids *grids, const dock_lig
         if (!e) {
             TimedLaunch tl;
             timing_begin(ctx, kernel_id(ctx, "dock_batch"), s, &tl);
-            lga_persistent<<<blocks, 32 * wpb, smem, s>>>(d_ligs, grids->dev, d_tasks, n_tasks, d_next, BC, scratch,
-                                                         floats_per_warp, gmax, smem_per_warp, best_geno, bE32, d_ev);
+            kern<<<blocks, 32 * wpb, smem, s>>>(d_ligs, grids->dev, d_tasks, n_tasks, d_next, BC, scratch,
+                                               floats_per_warp, gmax, smem_per_warp, best_geno, bE32, d_ev);
             timing_end(ctx, s, &tl);
             ++ctx->launches;
             e = cudaGetLastError();
@@ -392,8 +446,8 @@ lga_serve(const volatile ServeTask *tasks, const volatile ServeCtl *ctl, int cap
         const EvalLayout Yg = eval_layout(L.n_atoms, L.n_frag, L.nb8, true, 1);
         const WarpScratch S = warp_scratch(scratch, floats_per_warp, gw, pop_max, 7 + DOCK_MAX_TORSIONS);
         const int out = T->out;
-        const long long ev = dock_run_warp(L, G, C, P, ws, Yn, Yg, S, T->run, best_geno + (size_t)out * P.gstride,
-                                           best_E32 + out);
+        const long long ev = dock_run_warp<-1>(L, G, C, P, ws, Yn, Yg, S, T->run, best_geno + (size_t)out * P.gstride,
+                                               best_E32 + out);
         __syncwarp();
         if (lane == 0) {
             best_E[out] = rescore64_one(L, G, best_geno + (size_t)out * P.gstride);
@@ -524,6 +578,7 @@ int server_submit(dock_server *S, const dock_grids *grids, const dock_ligand *li
     if (P.pop_size < 2 || P.pop_size > S->pop_max || P.nruns < 1 || P.nruns > S->capacity || P.max_evals < 0 ||
         P.ls_count > P.pop_size || P.ls_iters < 0 || !(P.rho >= 0.f && P.rho < 1.f) || !(P.eps > 0.f))
         return set_err(ctx, DOCK_ERR_INVALID, "server_submit: invalid dock_params");
+    if (int rc0 = check_sw(ctx, P)) return rc0;
     if (lig->dev.n_atoms > S->max_atoms) return set_err(ctx, DOCK_ERR_SIZE, "server_submit: ligand above max_atoms");
     int rc = check_maps(ctx, grids, lig);
     if (rc) return rc;
@@ -532,19 +587,7 @@ int server_submit(dock_server *S, const dock_grids *grids, const dock_ligand *li
     for (long long t = std::max(0LL, first - S->capacity); t <= last - S->capacity; ++t)
         if (*(volatile long long *)&S->done[t % S->capacity] != t + 1)
             return set_err(ctx, DOCK_ERR_BUSY, "server_submit: queue full");
-    BatchConst BC;
-    BC.pop = P.pop_size;
-    BC.n_ls = P.ls_count;
-    BC.iters = P.ls_iters;
-    const long long per_gen = (long long)(P.pop_size - 1) + (long long)P.ls_count * P.ls_iters;
-    BC.ngen = P.max_evals > P.pop_size ? (P.max_evals - P.pop_size + per_gen - 1) / per_gen : 0;
-    BC.rho = P.rho;
-    BC.eps = P.eps;
-    BC.p_tour = P.p_tour;
-    BC.p_cross = P.p_cross;
-    BC.p_mut = P.p_mut;
-    BC.trans_mut = P.trans_mut;
-    BC.gstride = 7 + DOCK_MAX_TORSIONS;
+    const BatchConst BC = batch_const(P);
     for (int r = 0; r < P.nruns; ++r) {
         const long long t = first + r;
         ServeTask &T = S->tasks[t % S->capacity];

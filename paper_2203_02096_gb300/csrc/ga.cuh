@@ -1,5 +1,6 @@
-// ga.cuh -- genetic operators, local-search sampling and the ADADELTA
-// chain of the Lamarckian GA (paper, Section II-A), as warp-level device
+// ga.cuh -- genetic operators, local-search sampling and the two local
+// searches (ADADELTA; Solis-Wets, the paper's own) of the Lamarckian GA
+// (paper, Section II-A), as warp-level device
 // functions shared by the per-phase kernels (one docking, runs in parallel)
 // and the persistent batch kernel (one warp runs a whole docking run).
 //
@@ -16,7 +17,17 @@ namespace {
 constexpr int kMaxLs = 256;
 constexpr float kPiF = 3.14159265358979323846f;
 constexpr float kTwoPiF = 6.28318530717958647692f;
-enum : uint32_t { kInit = 1, kSelect = 2, kCross = 3, kMutate = 4, kLsPick = 5 };
+enum : uint32_t { kInit = 1, kSelect = 2, kCross = 3, kMutate = 4, kLsPick = 5, kSw = 6 };
+
+// Solis-Wets constants: step scale start / floor, expansion and contraction
+// factors, the runs of successes / failures that trigger them, deviation
+// half-widths per gene block at scale 1 (translation A, quaternion
+// component, torsion rad).
+struct SwConst {
+    float rho0, rho_lo, expand, contract;
+    int n_succ, n_fail;
+    float step_t, step_q, step_tau;
+};
 
 struct GaConst {
     int pop, nruns, nt;
@@ -286,5 +297,132 @@ __device__ float ls_chain(const LigandDev &L, const GridDev &G, float *ws, const
     return best;
 }
 
+
+// Torsion wrap to [-pi, pi) for any finite x, single rounded operations.
+__device__ __forceinline__ float wrap_any_rn(float x) {
+    const float k = floorf(__fdiv_rn(__fadd_rn(x, kPiF), kTwoPiF));
+    return __fsub_rn(x, __fmul_rn(kTwoPiF, k));
+}
+
+// Solis-Wets (Solis and Wets 1981: adaptive random search with a bias term)
+// from xi with energy e0 (NaN: evaluated first) by a team of W warps; warp 0
+// owns the genes (lane l: genes l and l + 32).  Each iteration draws
+//     d_j = b_j + rho * step(block of j) * u_j,   u_j uniform in [-1, 1)
+// (u_j: word j mod 4 of the Philox block (kSw << 16 | 10 it + j / 4, entity,
+// gen, run)), tries x + d, then x - d if that was not lower.  A success moves
+// x (b <- 0.2 b + 0.4 d forward, b <- b - 0.4 d backward), a failure halves
+// b; n_succ successes in a row scale rho by expand, n_fail failures by
+// contract.  Stops after iters iterations or once rho < rho_lo.  Gene
+// arithmetic is single rounded FP32 operations in a fixed order, so given
+// the same accept decisions any IEEE implementation reproduces the points.
+// Writes x (quaternion normalised) to xo, which may alias xi; returns its
+// energy; evals = energies computed.  Every thread of the team returns the
+// same values.
+template <int W>
+__device__ float sw_chain(const LigandDev &L, const GridDev &G, float *ws, const EvalLayout &Y, const dev::Team<W> &tm,
+                          const float *xi, float e0, float *xo, int iters, const SwConst &S, uint2 key, uint32_t run,
+                          uint32_t gen, uint32_t entity, long long &evals) {
+    const int Gn = L.n_genes;
+    const bool w0 = tm.warp() == 0;
+    const int lane = threadIdx.x & 31, j0 = lane, j1 = lane + 32;
+    const bool h0 = j0 < Gn, h1 = j1 < Gn;
+    float x0 = 0.f, x1 = 0.f, b0 = 0.f, b1 = 0.f, d0 = 0.f, d1 = 0.f, y0 = 0.f, y1 = 0.f;
+    if (w0) {
+        x0 = h0 ? xi[j0] : 0.f;
+        x1 = h1 ? xi[j1] : 0.f;
+    }
+    const float s0 = j0 < 3 ? S.step_t : (j0 < 7 ? S.step_q : S.step_tau), s1 = S.step_tau;
+    float *gs = ws + Y.geno;
+    long long n = 0;
+    float E = e0;
+    if (isnan(e0)) {
+        if (w0) {
+            if (h0) gs[j0] = x0;
+            if (h1) gs[j1] = x1;
+        }
+        E = dev::eval_team<W, false>(L, G, ws, Y, tm);
+        ++n;
+    }
+    float rho = S.rho0;
+    int ns = 0, nf = 0, it = 0;
+    for (; it < iters && rho >= S.rho_lo; ++it) {
+        if (w0) {
+            const float sr0 = __fmul_rn(rho, s0), sr1 = __fmul_rn(rho, s1);
+            const uint4 wa = draw4(key, run, gen, entity, kSw, (uint32_t)(10 * it + (j0 >> 2)));
+            d0 = __fadd_rn(b0, __fmul_rn(sr0, __fsub_rn(__fmul_rn(2.f, unif(word(wa, j0 & 3))), 1.f)));
+            if (h1) {
+                const uint4 wb = draw4(key, run, gen, entity, kSw, (uint32_t)(10 * it + (j1 >> 2)));
+                d1 = __fadd_rn(b1, __fmul_rn(sr1, __fsub_rn(__fmul_rn(2.f, unif(word(wb, j1 & 3))), 1.f)));
+            }
+            y0 = __fadd_rn(x0, d0);
+            y1 = __fadd_rn(x1, d1);
+            if (j0 >= 7) y0 = wrap_any_rn(y0);
+            y1 = wrap_any_rn(y1);
+            if (h0) gs[j0] = y0;
+            if (h1) gs[j1] = y1;
+        }
+        const float ef = dev::eval_team<W, false>(L, G, ws, Y, tm);
+        ++n;
+        bool ok = ef < E;
+        if (ok) {
+            E = ef;
+            if (w0) {
+                x0 = y0;
+                x1 = y1;
+                b0 = __fadd_rn(__fmul_rn(0.2f, b0), __fmul_rn(0.4f, d0));
+                b1 = __fadd_rn(__fmul_rn(0.2f, b1), __fmul_rn(0.4f, d1));
+            }
+        } else {
+            if (w0) {
+                y0 = __fsub_rn(x0, d0);
+                y1 = __fsub_rn(x1, d1);
+                if (j0 >= 7) y0 = wrap_any_rn(y0);
+                y1 = wrap_any_rn(y1);
+                if (h0) gs[j0] = y0;
+                if (h1) gs[j1] = y1;
+            }
+            const float eb = dev::eval_team<W, false>(L, G, ws, Y, tm);
+            ++n;
+            ok = eb < E;
+            if (ok) {
+                E = eb;
+                if (w0) {
+                    x0 = y0;
+                    x1 = y1;
+                    b0 = __fsub_rn(b0, __fmul_rn(0.4f, d0));
+                    b1 = __fsub_rn(b1, __fmul_rn(0.4f, d1));
+                }
+            } else if (w0) {
+                b0 = __fmul_rn(0.5f, b0);
+                b1 = __fmul_rn(0.5f, b1);
+            }
+        }
+        if (ok) {
+            ++ns;
+            nf = 0;
+        } else {
+            ++nf;
+            ns = 0;
+        }
+        if (ns >= S.n_succ) {
+            rho = __fmul_rn(rho, S.expand);
+            ns = 0;
+        } else if (nf >= S.n_fail) {
+            rho = __fmul_rn(rho, S.contract);
+            nf = 0;
+        }
+    }
+    if (w0) {
+        const float q3 = __shfl_sync(0xffffffffu, x0, 3), q4 = __shfl_sync(0xffffffffu, x0, 4);
+        const float q5 = __shfl_sync(0xffffffffu, x0, 5), q6 = __shfl_sync(0xffffffffu, x0, 6);
+        const float qn = __fsqrt_rn(__fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(q3, q3), __fmul_rn(q4, q4)), __fmul_rn(q5, q5)),
+                                              __fmul_rn(q6, q6)));
+        if (j0 >= 3 && j0 < 7 && qn > 0.f) x0 = __fdiv_rn(x0, qn);
+        if (h0) xo[j0] = x0;
+        if (h1) xo[j1] = x1;
+    }
+    evals = n;
+    return E;
+}
 
 }  // namespace

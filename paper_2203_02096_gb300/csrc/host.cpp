@@ -4,6 +4,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <queue>
 #include <string>
 #include <vector>
@@ -33,6 +34,26 @@ void *dev_alloc(dock_ctx *ctx, size_t bytes, cudaStream_t s) {
         return nullptr;
     }
     return p;
+}
+
+// Solis-Wets constants: finite, positive scales, at least one step in a
+// run, and iteration indices that fit the 16-bit draw field (10 it + 9).
+int check_sw(dock_ctx *ctx, const dock_params &p) {
+    if (p.ls_method != 0 && p.ls_method != 1) return set_err(ctx, DOCK_ERR_INVALID, "ls_method must be 0 or 1");
+    if (p.ls_method == 0) return DOCK_OK;
+    const bool ok = p.ls_iters <= 6553 && std::isfinite(p.sw_rho0) && p.sw_rho0 > 0.f && p.sw_rho_lo >= 0.f &&
+                    std::isfinite(p.sw_expand) && p.sw_expand > 0.f && p.sw_contract > 0.f && p.sw_contract < 1.f &&
+                    p.sw_succ >= 1 && p.sw_fail >= 1 && std::isfinite(p.sw_step[0]) && std::isfinite(p.sw_step[1]) &&
+                    std::isfinite(p.sw_step[2]) && p.sw_step[0] >= 0.f && p.sw_step[1] >= 0.f && p.sw_step[2] >= 0.f;
+    return ok ? DOCK_OK : set_err(ctx, DOCK_ERR_INVALID, "invalid Solis-Wets parameters (ls_iters <= 6553)");
+}
+
+long long *host_status(dock_ctx *ctx) {
+    if (!ctx->h_status && cudaHostAlloc((void **)&ctx->h_status, 2 * sizeof(long long), cudaHostAllocDefault)) {
+        cudaGetLastError();
+        ctx->h_status = nullptr;
+    }
+    return ctx->h_status;
 }
 
 void dev_free(dock_ctx *ctx, void *p, cudaStream_t s) {
@@ -114,6 +135,16 @@ void dock_default_params(dock_params *p) {
     p->p_mut = 0.02f;
     p->trans_mut = 2.0f;
     p->ls_threads = 0;
+    p->ls_method = 0;
+    p->sw_rho0 = 1.0f;
+    p->sw_rho_lo = 0.01f;
+    p->sw_expand = 2.0f;
+    p->sw_contract = 0.5f;
+    p->sw_succ = 4;
+    p->sw_fail = 4;
+    p->sw_step[0] = 1.0f;
+    p->sw_step[1] = 0.2f;
+    p->sw_step[2] = 0.75f;
 }
 
 int dock_create(dock_ctx **out, int device, const dock_allocator *alloc) {
@@ -143,6 +174,7 @@ int dock_destroy(dock_ctx *ctx) {
     if (!ctx) return DOCK_ERR_INVALID;
     flush_timing(ctx, false);
     for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
+    if (ctx->h_status) cudaFreeHost(ctx->h_status);
     delete ctx;
     return DOCK_OK;
 }

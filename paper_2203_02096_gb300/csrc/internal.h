@@ -119,6 +119,7 @@ struct dock_ctx {
     std::vector<int64_t> kernel_launches;
     int64_t launches = 0;
     int *d_flag = nullptr;  // device error word: 0 = fine
+    long long *h_status = nullptr;  // pinned host words read back by the Solis-Wets docking loop
 };
 
 struct dock_grids {
@@ -144,6 +145,8 @@ int cuda_err(dock_ctx *ctx, cudaError_t e, const char *what);
 void *dev_alloc(dock_ctx *ctx, size_t bytes, cudaStream_t s);
 void dev_free(dock_ctx *ctx, void *p, cudaStream_t s);
 int kernel_id(dock_ctx *ctx, const char *name);
+long long *host_status(dock_ctx *ctx);
+int check_sw(dock_ctx *ctx, const dock_params &p);  // ls_method and Solis-Wets constants  // 2 pinned words, allocated on first use; NULL on failure
 void timing_begin(dock_ctx *ctx, int kid, cudaStream_t s, TimedLaunch *tl);
 void timing_end(dock_ctx *ctx, cudaStream_t s, TimedLaunch *tl);
 int check_maps(dock_ctx *ctx, const dock_grids *g, const dock_ligand *l);

@@ -1,15 +1,17 @@
 // search.cu -- the Lamarckian genetic algorithm on the device (paper,
 // Section II-A): initial population, elitism + tournament selection +
-// two-point crossover + mutation, local-search sampling, ADADELTA local
-// search with Lamarckian write-back, per-run evaluation counting (the
-// per-run sum of Listing 1, folded into the kernels), and the driver that
-// runs generations until the budget is spent.
+// two-point crossover + mutation, local-search sampling, the local search
+// (ADADELTA, or the paper's Solis-Wets) with Lamarckian write-back, per-run
+// evaluation counting (the per-run sum of Listing 1, folded into the
+// kernels), and the driver that runs generations until the budget is spent.
 //
 // Genetic operators act on FP32 genes with one IEEE round-to-nearest
 // operation per step (__fadd_rn & co., never contracted), so that given the
 // same energies and the same Philox stream they are reproducible exactly by
 // any IEEE single-precision implementation.
 #include <math.h>
+
+#include <cmath>
 
 #include <algorithm>
 #include <mutex>
@@ -47,7 +49,7 @@ template <bool EVAL>
 __global__ void __launch_bounds__(128)
 ga_kernel(LigandDev L, GridDev G, GaConst C, uint32_t gen, const float *__restrict__ pop_old,
           const float *__restrict__ E_old, float *__restrict__ pop_new, float *__restrict__ E_new,
-          long long *info, unsigned long long *evals, EvalLayout W) {
+          long long *info, unsigned long long *evals, const int *__restrict__ active, EvalLayout W) {
     extern __shared__ float4 smem4[];
     float *ws = reinterpret_cast<float *>(smem4) + (threadIdx.x >> 5) * W.total;
     const int lane = threadIdx.x & 31;
@@ -59,6 +61,11 @@ ga_kernel(LigandDev L, GridDev G, GaConst C, uint32_t gen, const float *__restri
     const float *Eo = E_old + (size_t)r * C.pop;
     float *child = pop_new + (size_t)item * Gn;
     float *gs = ws + W.geno;
+    if (active && !active[r]) {  // run finished: carry its population over unchanged
+        for (int j = lane; j < Gn; j += 32) child[j] = old[(size_t)s * Gn + j];
+        if (lane == 0 && E_new) E_new[item] = Eo[s];
+        return;
+    }
     if (s == 0) {  // elitism: the best old individual, not re-evaluated
         float be;
         const int bi = run_argmin(Eo, C.pop, lane, be);
@@ -87,9 +94,10 @@ ga_kernel(LigandDev L, GridDev G, GaConst C, uint32_t gen, const float *__restri
 // The local-search sample of a generation: the first n_ls entries of a
 // partial Fisher-Yates shuffle of 0..pop-1, kept as a list of displaced
 // positions instead of a pop-sized array.
-__global__ void picks_kernel(int pop, int n_ls, int nruns, uint2 key, uint32_t gen, int *picks) {
+__global__ void picks_kernel(int pop, int n_ls, int nruns, uint2 key, uint32_t gen, int *picks,
+                             const int *__restrict__ active) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= nruns) return;
+    if (r >= nruns || (active && !active[r])) return;
     ls_picks_one(pop, n_ls, key, (uint32_t)r, gen, picks + r * n_ls);
 }
 
@@ -127,6 +135,81 @@ ls_kernel(LigandDev L, GridDev G, float *x_in, float *E_pop, const int *__restri
     if (tm.rank == 0) {
         *eo = best;
         if (evals) atomicAdd(evals + run, (unsigned long long)iters);
+    }
+}
+
+// Solis-Wets local search, one team of W warps per chain, as ls_kernel.
+// With picks (inside dock): chain c is pick k = c % n_ls of run c / n_ls,
+// starting from the individual and its stored energy, updated in place,
+// entity k of the run's generation gen in the random stream; runs with
+// active[run] == 0 are skipped.  Without picks: chain c starts at x_in[c]
+// (energy E0[c], or evaluated when E0 is null), entity c of (run0, gen),
+// and writes x_out[c], E_out[c], evals_out[c].
+template <int W>
+__global__ void __launch_bounds__(W == 1 ? 128 : 32 * W, W == 8 ? 3 : W == 4 ? 4 : W == 2 ? 8 : 4)
+sw_kernel(LigandDev L, GridDev G, float *x_in, float *E_pop, const int *__restrict__ picks, int pop, int n_ls,
+          int nchains, int iters, SwConst S, uint2 key, uint32_t run0, uint32_t gen, const float *__restrict__ E0,
+          float *x_out, float *E_out, unsigned long long *evals, long long *evals_out, const int *__restrict__ active,
+          EvalLayout Y) {
+    extern __shared__ float4 smem4[];
+    const int team_in_block = W == 1 ? (threadIdx.x >> 5) : 0;
+    float *ws = reinterpret_cast<float *>(smem4) + team_in_block * Y.total;
+    const dev::Team<W> tm(W == 1 ? (threadIdx.x & 31) : threadIdx.x);
+    const int c = W == 1 ? blockIdx.x * (blockDim.x >> 5) + team_in_block : blockIdx.x;
+    if (c >= nchains) return;  // uniform over the team
+    const int Gn = L.n_genes;
+    float *xi, *xo, *eo;
+    float e0;
+    uint32_t run = run0, entity = (uint32_t)c;
+    if (picks) {
+        run = (uint32_t)(c / n_ls);
+        entity = (uint32_t)(c % n_ls);
+        if (active && !active[run]) return;
+        const int ind = __ldg(picks + c);
+        xi = x_in + ((size_t)run * pop + ind) * Gn;
+        xo = xi;
+        eo = E_pop + (size_t)run * pop + ind;
+        e0 = *eo;
+    } else {
+        xi = x_in + (size_t)c * Gn;
+        xo = x_out + (size_t)c * Gn;
+        eo = E_out + c;
+        e0 = E0 ? __ldg(E0 + c) : __int_as_float(0x7fc00000);
+    }
+    long long n = 0;
+    const float best = sw_chain<W>(L, G, ws, Y, tm, xi, e0, xo, iters, S, key, run, gen, entity, n);
+    if (tm.rank == 0) {
+        *eo = best;
+        if (evals) atomicAdd(evals + (picks ? run : 0), (unsigned long long)n);
+        if (evals_out) evals_out[c] = n;
+    }
+}
+
+// After a generation of a Solis-Wets docking: run r stays active while its
+// evaluation count is below the budget; status = (active runs, least count
+// among them).  One block.
+__global__ void gate_kernel(const unsigned long long *__restrict__ evals, int R, long long max_evals, int *active,
+                            long long *status) {
+    __shared__ int cnt;
+    __shared__ unsigned long long lo;
+    if (threadIdx.x == 0) {
+        cnt = 0;
+        lo = ~0ull;
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < R; r += blockDim.x) {
+        const unsigned long long e = evals[r];
+        const int a = e < (unsigned long long)max_evals;
+        active[r] = a;
+        if (a) {
+            atomicAdd(&cnt, 1);
+            atomicMin(&lo, e);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        status[0] = cnt;
+        status[1] = cnt ? (long long)lo : 0;
     }
 }
 
@@ -208,7 +291,21 @@ int resolve_params(dock_ctx *ctx, const dock_params *in, dock_params &p) {
     if (p.pop_size < 2 || p.pop_size > (1 << 20) || p.nruns < 1 || p.max_evals < 0 || p.ls_count > p.pop_size ||
         p.ls_count > kMaxLs || p.ls_iters < 0 || !(p.rho >= 0.f && p.rho < 1.f) || !(p.eps > 0.f))
         return set_err(ctx, DOCK_ERR_INVALID, "invalid dock_params");
-    return DOCK_OK;
+    return check_sw(ctx, p);
+}
+
+SwConst sw_const(const dock_params &p) {
+    SwConst S;
+    S.rho0 = p.sw_rho0;
+    S.rho_lo = p.sw_rho_lo;
+    S.expand = p.sw_expand;
+    S.contract = p.sw_contract;
+    S.n_succ = p.sw_succ;
+    S.n_fail = p.sw_fail;
+    S.step_t = p.sw_step[0];
+    S.step_q = p.sw_step[1];
+    S.step_tau = p.sw_step[2];
+    return S;
 }
 
 // Warps per local-search chain: threads_req (32..256) when given, else
@@ -227,14 +324,16 @@ int ls_team_warps(const dock_ctx *ctx, int chains, int threads_req, const Ligand
     return w;
 }
 
-// Launches ls_kernel<W>.  W = 1: four one-warp teams per block once the
-// chains cover every SM several times, else one; W > 1: one team per block.
-cudaError_t launch_ls(dock_ctx *ctx, int W, int chains, const EvalLayout &Y, cudaStream_t s, const char *name,
-                      void **args) {
+// Launches a local-search kernel at team width W (k1..k8: its W = 1, 2, 4,
+// 8 instances).  W = 1: four one-warp teams per block once the chains cover
+// every SM several times, else one; W > 1: one team per block.
+template <typename K1, typename K2, typename K4, typename K8>
+cudaError_t launch_team(dock_ctx *ctx, int W, int chains, const EvalLayout &Y, cudaStream_t s, const char *name,
+                        void **args, K1 k1, K2 k2, K4 k4, K8 k8) {
     if (chains <= 0) return cudaSuccess;
     if (W == 1) {
         const int wpb = chains >= 8 * ctx->num_sms && evaluator_smem_ok(ctx, Y, 4) ? 4 : 1;
-        return launch_items(ctx, ls_kernel<1>, chains, wpb, (size_t)Y.total * 4 * wpb, s, name, args);
+        return launch_items(ctx, k1, chains, wpb, (size_t)Y.total * 4 * wpb, s, name, args);
     }
     const size_t smem = (size_t)Y.total * 4;
     // one team per block: launch_items with "warps per item" = W
@@ -250,9 +349,19 @@ cudaError_t launch_ls(dock_ctx *ctx, int W, int chains, const EvalLayout &Y, cud
         ++ctx->launches;
         return e;
     };
-    if (W == 2) return go(ls_kernel<2>);
-    if (W == 4) return go(ls_kernel<4>);
-    return go(ls_kernel<8>);
+    if (W == 2) return go(k2);
+    if (W == 4) return go(k4);
+    return go(k8);
+}
+
+cudaError_t launch_ls(dock_ctx *ctx, int W, int chains, const EvalLayout &Y, cudaStream_t s, const char *name,
+                      void **args) {
+    return launch_team(ctx, W, chains, Y, s, name, args, ls_kernel<1>, ls_kernel<2>, ls_kernel<4>, ls_kernel<8>);
+}
+
+cudaError_t launch_sw(dock_ctx *ctx, int W, int chains, const EvalLayout &Y, cudaStream_t s, const char *name,
+                      void **args) {
+    return launch_team(ctx, W, chains, Y, s, name, args, sw_kernel<1>, sw_kernel<2>, sw_kernel<4>, sw_kernel<8>);
 }
 
 }  // namespace
@@ -296,31 +405,90 @@ int dock_async(dock_ctx *ctx, const dock_grids *grids, const dock_ligand *lig, c
             void *a[] = {&l, &g, &C, &popA, &EA, &ev, &wn};
             if (!e) e = launch_items(ctx, init_kernel<true>, (int)items, gw, (size_t)Wn.total * 4 * gw, s, "dock_init", a);
         }
-        const long long per_gen = (long long)(pop - 1) + (long long)nls * P.ls_iters;
-        long long ngen = 0;
-        if (P.max_evals > pop) ngen = (P.max_evals - pop + per_gen - 1) / per_gen;
         const int chains = R * nls;
         long long *no_info = nullptr;
         float *no_out = nullptr;
-        for (long long gen = 1; gen <= ngen && !e; ++gen) {
-            uint32_t g32 = (uint32_t)gen;
-            void *a[] = {&l, &g, &C, &g32, &popA, &EA, &popB, &EB, &no_info, &ev, &wn};
-            e = launch_items(ctx, ga_kernel<true>, (int)items, gw, (size_t)Wn.total * 4 * gw, s, "dock_ga", a);
-            if (!e && chains > 0 && P.ls_iters > 0) {
-                TimedLaunch tl;
-                timing_begin(ctx, kernel_id(ctx, "dock_picks"), s, &tl);
-                picks_kernel<<<(R + 63) / 64, 64, 0, s>>>(pop, nls, R, C.key, g32, picks);
-                timing_end(ctx, s, &tl);
+        int *no_active = nullptr;
+        if (P.ls_method == 0) {
+            const long long per_gen = (long long)(pop - 1) + (long long)nls * P.ls_iters;
+            long long ngen = 0;
+            if (P.max_evals > pop) ngen = (P.max_evals - pop + per_gen - 1) / per_gen;
+            for (long long gen = 1; gen <= ngen && !e; ++gen) {
+                uint32_t g32 = (uint32_t)gen;
+                void *a[] = {&l, &g, &C, &g32, &popA, &EA, &popB, &EB, &no_info, &ev, &no_active, &wn};
+                e = launch_items(ctx, ga_kernel<true>, (int)items, gw, (size_t)Wn.total * 4 * gw, s, "dock_ga", a);
+                if (!e && chains > 0 && P.ls_iters > 0) {
+                    TimedLaunch tl;
+                    timing_begin(ctx, kernel_id(ctx, "dock_picks"), s, &tl);
+                    picks_kernel<<<(R + 63) / 64, 64, 0, s>>>(pop, nls, R, C.key, g32, picks, no_active);
+                    timing_end(ctx, s, &tl);
+                    ++ctx->launches;
+                    e = cudaGetLastError();
+                    int iters = P.ls_iters;
+                    float rho = P.rho, eps = P.eps;
+                    int nl = nls, ch = chains, popn = pop;
+                    void *c[] = {&l, &g, &popB, &EB, &picks, &popn, &nl, &ch, &iters, &rho, &eps, &no_out, &no_out, &ev, &wg};
+                    if (!e) e = launch_ls(ctx, lw, chains, Wg, s, "dock_ls", c);
+                }
+                std::swap(popA, popB);
+                std::swap(EA, EB);
+            }
+        } else if (P.max_evals > pop) {
+            // Solis-Wets: a run's count per generation depends on its searches,
+            // so runs are gated on the device and the host queues generations
+            // in chunks, reading (active runs, least count) after each.
+            const EvalLayout Ws = eval_layout(L.n_atoms, L.n_frag, L.nb8, false, lw);
+            int *active = (int *)dev_alloc(ctx, (size_t)R * 4, s);
+            long long *status = (long long *)dev_alloc(ctx, 16, s);
+            long long *h = host_status(ctx);
+            if (!active || !status || !h) {
+                rc = set_err(ctx, DOCK_ERR_OOM, "allocation failed in dock (Solis-Wets state)");
+            } else {
+                SwConst S = sw_const(P);
+                const long long per_gen_hi = (long long)(pop - 1) + 2LL * nls * P.ls_iters;
+                const long long cap = P.max_evals / (pop - 1) + 2;  // each generation adds >= pop - 1
+                long long gen = 0, chunk = std::max(1LL, (P.max_evals - pop) / per_gen_hi);
+                const long long mx = P.max_evals;
+                gate_kernel<<<1, 256, 0, s>>>(ev, R, mx, active, status);
                 ++ctx->launches;
                 e = cudaGetLastError();
-                int iters = P.ls_iters;
-                float rho = P.rho, eps = P.eps;
-                int nl = nls, ch = chains, popn = pop;
-                void *c[] = {&l, &g, &popB, &EB, &picks, &popn, &nl, &ch, &iters, &rho, &eps, &no_out, &no_out, &ev, &wg};
-                if (!e) e = launch_ls(ctx, lw, chains, Wg, s, "dock_ls", c);
+                while (!e && gen < cap) {
+                    for (long long i = 0; i < chunk && gen < cap && !e; ++i) {
+                        ++gen;
+                        uint32_t g32 = (uint32_t)gen;
+                        void *a[] = {&l, &g, &C, &g32, &popA, &EA, &popB, &EB, &no_info, &ev, &active, &wn};
+                        e = launch_items(ctx, ga_kernel<true>, (int)items, gw, (size_t)Wn.total * 4 * gw, s, "dock_ga", a);
+                        if (!e && chains > 0 && P.ls_iters > 0) {
+                            picks_kernel<<<(R + 63) / 64, 64, 0, s>>>(pop, nls, R, C.key, g32, picks, active);
+                            ++ctx->launches;
+                            e = cudaGetLastError();
+                            int iters = P.ls_iters, nl = nls, ch = chains, popn = pop;
+                            uint32_t run0 = 0;
+                            const float *no_e0 = nullptr;
+                            long long *no_eo = nullptr;
+                            EvalLayout ws_ = Ws;
+                            void *c[] = {&l, &g, &popB, &EB, &picks, &popn, &nl, &ch, &iters, &S, &C.key, &run0, &g32,
+                                         &no_e0, &no_out, &no_out, &ev, &no_eo, &active, &ws_};
+                            if (!e) e = launch_sw(ctx, lw, chains, Ws, s, "dock_sw", c);
+                        }
+                        if (!e) {
+                            gate_kernel<<<1, 256, 0, s>>>(ev, R, mx, active, status);
+                            ++ctx->launches;
+                            e = cudaGetLastError();
+                        }
+                        std::swap(popA, popB);
+                        std::swap(EA, EB);
+                    }
+                    if (!e) e = cudaMemcpyAsync(h, status, 16, cudaMemcpyDeviceToHost, s);
+                    if (!e) e = cudaStreamSynchronize(s);
+                    if (e || h[0] == 0) break;
+                    // the least-advanced run's mean count per generation so far
+                    const double rate = std::max(1.0, (double)(h[1] - pop) / (double)gen);
+                    chunk = std::max(1LL, (long long)std::ceil((double)(P.max_evals - h[1]) / rate));
+                }
             }
-            std::swap(popA, popB);
-            std::swap(EA, EB);
+            dev_free(ctx, active, s);
+            dev_free(ctx, status, s);
         }
         if (!e) {
             TimedLaunch tl;
@@ -413,7 +581,8 @@ int dock_ga_children(dock_ctx *ctx, int n_torsions, int pop, int nruns, const fl
     float *no_e = nullptr;
     unsigned long long *no_ev = nullptr;
     long long *inf = (long long *)info;
-    void *a[] = {&l, &g, &C, &generation, &pop_old, &E_old, &pop_new, &no_e, &inf, &no_ev, &w};
+    const int *no_active = nullptr;
+    void *a[] = {&l, &g, &C, &generation, &pop_old, &E_old, &pop_new, &no_e, &inf, &no_ev, &no_active, &w};
     cudaError_t e = launch_items(ctx, ga_kernel<false>, pop * nruns, 4, (size_t)w.total * 16, (cudaStream_t)stream,
                                  "ga_children", a);
     return e ? cuda_err(ctx, e, "ga kernel") : DOCK_OK;
@@ -425,7 +594,8 @@ int dock_ls_picks(dock_ctx *ctx, int pop, int n_ls, int nruns, uint64_t seed, ui
         return ctx ? set_err(ctx, DOCK_ERR_INVALID, "invalid argument") : DOCK_ERR_INVALID;
     if (n_ls == 0) return DOCK_OK;
     const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
-    picks_kernel<<<(nruns + 63) / 64, 64, 0, (cudaStream_t)stream>>>(pop, n_ls, nruns, key, generation, picks);
+    picks_kernel<<<(nruns + 63) / 64, 64, 0, (cudaStream_t)stream>>>(pop, n_ls, nruns, key, generation, picks,
+                                                                     nullptr);
     ++ctx->launches;
     cudaError_t e = cudaGetLastError();
     return e ? cuda_err(ctx, e, "picks kernel") : DOCK_OK;
@@ -455,6 +625,42 @@ int dock_local_search(dock_ctx *ctx, const dock_grids *grids, const dock_ligand 
     void *a[] = {&l, &g, &xin, &no_pop, &no_picks, &zero, &one, &B, &iters, &rho, &eps, &x_best, &E_best, &no_ev, &W};
     cudaError_t e = launch_ls(ctx, lw, B, W, (cudaStream_t)stream, "local_search", a);
     return e ? cuda_err(ctx, e, "local search kernel") : DOCK_OK;
+}
+
+int dock_solis_wets(dock_ctx *ctx, const dock_grids *grids, const dock_ligand *lig, const float *x0,
+                    const float *E0, int B, const dock_params *params, uint64_t seed, uint32_t run,
+                    uint32_t generation, float *x_best, float *E_best, int64_t *evals, void *stream) {
+    if (!ctx || !grids || !lig || B < 0 || (B > 0 && (!x0 || !x_best || !E_best)))
+        return ctx ? set_err(ctx, DOCK_ERR_INVALID, "invalid argument") : DOCK_ERR_INVALID;
+    dock_params P;
+    if (params) P = *params;
+    else dock_default_params(&P);
+    P.ls_method = 1;
+    if (P.ls_threads != 0 && P.ls_threads != 32 && P.ls_threads != 64 && P.ls_threads != 128 && P.ls_threads != 256)
+        return set_err(ctx, DOCK_ERR_INVALID, "ls_threads must be 0, 32, 64, 128 or 256");
+    if (P.ls_iters < 0) return set_err(ctx, DOCK_ERR_INVALID, "ls_iters must be >= 0");
+    int rc = check_sw(ctx, P);
+    if (rc) return rc;
+    if ((rc = check_maps(ctx, grids, lig))) return rc;
+    if (B == 0) return DOCK_OK;
+    const LigandDev &L = lig->dev;
+    const int lw = ls_team_warps(ctx, B, P.ls_threads, L);
+    EvalLayout W = eval_layout(L.n_atoms, L.n_frag, L.nb8, false, lw);
+    if (!evaluator_smem_ok(ctx, W, 1)) return set_err(ctx, DOCK_ERR_SIZE, "ligand too large for shared memory");
+    LigandDev l = L;
+    GridDev g = grids->dev;
+    float *xin = const_cast<float *>(x0);
+    float *no_pop = nullptr;
+    const int *no_picks = nullptr, *no_active = nullptr;
+    unsigned long long *no_ev = nullptr;
+    long long *eo = (long long *)evals;
+    int zero = 0, one = 1, iters = P.ls_iters;
+    SwConst S = sw_const(P);
+    uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+    void *a[] = {&l, &g, &xin, &no_pop, &no_picks, &zero, &one, &B, &iters, &S, &key, &run, &generation, &E0,
+                 &x_best, &E_best, &no_ev, &eo, &no_active, &W};
+    cudaError_t e = launch_sw(ctx, lw, B, W, (cudaStream_t)stream, "solis_wets", a);
+    return e ? cuda_err(ctx, e, "Solis-Wets kernel") : DOCK_OK;
 }
 
 int dock_philox(dock_ctx *ctx, const uint32_t *ctr, int n, uint32_t key_lo, uint32_t key_hi, uint32_t *out,
@@ -514,6 +720,7 @@ extern "C" int dock_async_noalloc(dock_ctx *ctx, const dock_grids *grids, const 
     dock_params P;
     int rc = resolve_params(ctx, params, P);
     if (rc) return rc;
+    if (P.ls_method != 0) return set_err(ctx, DOCK_ERR_INVALID, "dock_async_noalloc runs the ADADELTA search only");
     if ((rc = check_maps(ctx, grids, lig))) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     const LigandDev &L = lig->dev;
@@ -561,10 +768,11 @@ extern "C" int dock_async_noalloc(dock_ctx *ctx, const dock_grids *grids, const 
     float *no_out = nullptr;
     for (long long gen = 1; gen <= ngen && !e; ++gen) {
         uint32_t g32 = (uint32_t)gen;
-        void *a[] = {&l, &g, &C, &g32, &popA, &EA, &popB, &EB, &no_info, &ev, &wn};
+        const int *no_active = nullptr;
+        void *a[] = {&l, &g, &C, &g32, &popA, &EA, &popB, &EB, &no_info, &ev, &no_active, &wn};
         e = launch_items(ctx, ga_kernel<true>, (int)items, gw, (size_t)Wn.total * 4 * gw, s, "dock_ga", a);
         if (!e && chains > 0 && P.ls_iters > 0) {
-            picks_kernel<<<(R + 63) / 64, 64, 0, s>>>(pop, nls, R, C.key, g32, picks);
+            picks_kernel<<<(R + 63) / 64, 64, 0, s>>>(pop, nls, R, C.key, g32, picks, nullptr);
             ++ctx->launches;
             e = cudaGetLastError();
             int iters = P.ls_iters;

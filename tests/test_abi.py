@@ -40,3 +40,27 @@ def test_product_never_imports_the_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(import|from)\s+oracle\b", text, flags=re.M), f
                 assert "liboracle" not in text and "oracle.c" not in text, f
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """dock_params and dock_allocator: the binding's ctypes layout (size and
+    every field offset) is the C compiler's."""
+    import subprocess
+    from paper_2203_02096_gb300 import capi
+    checks = [("dock_params", capi.DockParams), ("dock_allocator", capi.DockAllocator)]
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "dock.h"', "int main(void) {"]
+    for cname, cls in checks:
+        lines.append(f'printf("%zu\\n", sizeof({cname}));')
+        for f in cls._fields_:
+            lines.append(f'printf("%zu\\n", offsetof({cname}, {f[0]}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    want = []
+    for _, cls in checks:
+        want.append(ctypes.sizeof(cls))
+        want += [getattr(cls, f[0]).offset for f in cls._fields_]
+    assert got == want
