@@ -217,7 +217,7 @@ def run(args):
     import torch
     import torch.distributed as dist
 
-    from paper_2203_02096_gb300 import capi
+    from paper_2203_02096_gb300 import autotune, capi
 
     rank, world, local = dist_env()
     if world > 1:
@@ -230,7 +230,11 @@ def run(args):
     G = capi.grids_from_receptor(ctx, w.receptor, w.box)
     L = capi.ligand_from(ctx, w.ligand)
     P = capi.default_params(pop_size=w.pop_size, nruns=w.nruns, max_evals=w.max_evals, ls_iters=w.ls_iters,
-                            ls_threads=args.ls_threads)
+                            ls_threads=max(args.ls_threads, 0))
+    tune_dir = tempfile.mkdtemp(prefix="dock_tune_")
+    tuner = autotune.Tuner(ctx, path=os.path.join(tune_dir, "tune.json"))
+    if args.ls_threads < 0:      # the autotuner picks the threads per local-search chain (untimed)
+        P = tuner.tuned(G, L, P)
     seed = replica_seed(w.seed, rank)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -302,6 +306,7 @@ def run(args):
     multi = batched_docking(ctx, dev) if not args.no_batch else None
     serving = serving_sweep(ctx, dev) if not args.no_batch else None
     solis = solis_wets_vs_adadelta(ctx, G, L, w, dev, out, value) if not args.no_batch else None
+    tuning = tuning_curves(ctx, G, w, tuner, P) if not args.no_batch else None
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -314,7 +319,8 @@ def run(args):
             "warmup": args.warmup, "ms_per_step": float(np.mean(step_ms)), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": dict(config_dict(w, "flushed between steps (256 MB write, outside the step events)"),
-                           ls_threads=args.ls_threads or "auto"),
+                           ls_threads=f"{P.ls_threads} (autotuned)" if args.ls_threads < 0 else
+                           (args.ls_threads or "library default")),
             "ligands_per_hour": ligands_per_hour,
             "roofline": {"bound": "alu", "kernel": "dock_ls (ADADELTA local search)", "achieved": achieved,
                          "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
@@ -334,6 +340,7 @@ def run(args):
             "batched_docking": multi,
             "serving": serving,
             "solis_wets": solis,
+            "tuning": tuning,
             "best_energy_median": float(np.median(out["best_E"].cpu().numpy())),
         }
         print(json.dumps(line), flush=True)
@@ -393,7 +400,7 @@ def batched_docking(ctx, dev, n_ligs: int = 1024, nruns: int = 20, evals_per_run
     evaluation does not depend on the budget)."""
     import torch
 
-    from paper_2203_02096_gb300 import capi, synth
+    from paper_2203_02096_gb300 import autotune, capi, synth
     rng = np.random.default_rng(3)
     ligs = [synth.make_ligand(int(rng.integers(10, 109)), int(rng.integers(0, 33)), seed=5000 + k)
             for k in range(n_ligs)]
@@ -402,20 +409,26 @@ def batched_docking(ctx, dev, n_ligs: int = 1024, nruns: int = 20, evals_per_run
     L = [capi.ligand_from(ctx, l) for l in ligs]
     P = capi.default_params(pop_size=150, nruns=nruns, max_evals=evals_per_run, ls_iters=100)
     seeds = np.arange(n_ligs, dtype=np.uint64)
-    capi.dock_batch(ctx, G, L[:8], P, seeds[:8])          # warm-up
+    # warps per block of the persistent kernel by the autotuner (one-generation probes)
+    tuner = autotune.Tuner(ctx, path=os.path.join(tempfile.mkdtemp(prefix="dock_tune_"), "tune.json"))
+    Pb = capi.DockParams.from_buffer_copy(P)
+    Pb.batch_warps = tuner.batch_warps(G, L, P, probe_generations=1)
+    capi.dock_batch(ctx, G, L[:8], Pb, seeds[:8])          # warm-up
     torch.cuda.synchronize(dev)
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record()
-    out = capi.dock_batch(ctx, G, L, P, seeds)
+    out = capi.dock_batch(ctx, G, L, Pb, seeds)
     b.record()
     torch.cuda.synchronize(dev)
     t_batch = a.elapsed_time(b) / 1e3
     ev_batch = int(out["evals"].sum().item())
     # plain form on a sample of the same ligands, one docking at a time
-    t0 = time.perf_counter()
     ev_plain = 0
+    plain_params = [tuner.tuned(G, L[k], P) for k in range(n_plain)]   # threads per chain, per ligand
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
     for k in range(n_plain):
-        _, _, ev = capi.dock(ctx, G, L[k], P, int(seeds[k]))
+        _, _, ev = capi.dock(ctx, G, L[k], plain_params[k], int(seeds[k]))
         ev_plain += int(ev.sum())
     torch.cuda.synchronize(dev)
     t_plain = time.perf_counter() - t0
@@ -429,7 +442,9 @@ def batched_docking(ctx, dev, n_ligs: int = 1024, nruns: int = 20, evals_per_run
             "batched_evals_per_s": rate_b, "plain_evals_per_s": rate_p, "speedup": rate_b / rate_p,
             "batched_ligands_per_hour_extrapolated": 3600.0 * rate_b / per_lig_full,
             "plain_ligands_per_hour_extrapolated": 3600.0 * rate_p / per_lig_full,
-            "batch_seconds": t_batch, "launches": 1}
+            "batch_seconds": t_batch, "launches": 1,
+            "autotuned": {"batch_warps": int(Pb.batch_warps), "batch_warps_ms": tuner.curve("|batch|"),
+                          "plain_ls_threads": [int(p.ls_threads) for p in plain_params]}}
 
 
 def serving_sweep(ctx, dev, rates=(10, 30, 100, 300, 1000), seconds: float = 2.0, nruns: int = 20,
@@ -484,6 +499,24 @@ def serving_sweep(ctx, dev, rates=(10, 30, 100, 300, 1000), seconds: float = 2.0
             "sweep": out,
             "plain": {"requests_per_s": n_plain / t_plain, "ligands_per_hour": 3600.0 * n_plain / t_plain,
                       "latency_s_median": float(np.median(lat))}}
+
+
+def tuning_curves(ctx, G, w, tuner, P_head):
+    """The paper's tuning study (Section V-B: threads per block) on GB300:
+    device time of the drug-size workload's local-search launch (50 runs x 9
+    chains, 50 ADADELTA iterations) at 32..256 threads per chain, for ligands
+    of the paper's three sizes (21/2, 43/15, 108/31 atoms/torsions, synthetic
+    stand-ins), and the width the autotuner chose for the headline."""
+    from paper_2203_02096_gb300 import autotune, capi, synth
+    out = {}
+    for name, (na, nt) in {"21 atoms / 2 torsions": (21, 2), "43 atoms / 15 torsions": (43, 15),
+                           "108 atoms / 31 torsions": (108, 31)}.items():
+        lig = capi.ligand_from(ctx, synth.make_ligand(na, nt, seed=77))
+        P = capi.default_params(pop_size=w.pop_size, nruns=w.nruns, max_evals=w.max_evals, ls_iters=w.ls_iters)
+        out[name] = {str(k): v for k, v in autotune.ls_curve(ctx, G, lig, P).items()}
+        lig.free()
+    return {"ls_threads_curve": out, "headline_ls_threads": int(P_head.ls_threads),
+            "headline_tuning_ms": tuner.curve("|ls|")}
 
 
 def solis_wets_vs_adadelta(ctx, G, L, w, dev, ada_out, ada_value):
@@ -589,7 +622,8 @@ def main(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the score_grad_batch side measurement")
-    ap.add_argument("--ls-threads", type=int, default=0, help="threads per local-search chain (0 = auto)")
+    ap.add_argument("--ls-threads", type=int, default=-1,
+                    help="threads per local-search chain (-1 = autotuned, 0 = library default)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

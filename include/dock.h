@@ -100,6 +100,9 @@ typedef struct {
     int sw_succ, sw_fail; /* default 4, 4                                          */
     float sw_step[3];  /* deviation half-widths at scale 1: translation (A) 1.0,
                           quaternion component 0.2, torsion (rad) 0.75             */
+    int batch_warps;   /* warps per block of dock_batch's persistent kernel: 1, 2,
+                          4, or 0 = as many (<= 4) as shared memory allows;
+                          results do not depend on it; default 0                */
 } dock_params;
 
 /* Library version (major*10000 + minor*100 + patch). */
@@ -214,6 +217,24 @@ int dock_async(dock_ctx *ctx, const dock_grids *grids, const dock_ligand *lig, c
 int dock_batch(dock_ctx *ctx, const dock_grids *grids, const dock_ligand *const *ligs, int n_ligs,
                const dock_params *params, const uint64_t *seeds, float *best_geno, float *best_E32, double *best_E,
                int64_t *evals_used, void *stream);
+
+/* ---- autotuning: device time of candidate launch shapes ----
+ * dock_tune times the kernel family `what` at each candidate launch shape
+ * cand[0..n_cand-1] on the given inputs, `reps` launches each after one
+ * untimed launch, and writes the mean device milliseconds per launch to
+ * ms[i] (-1 where the candidate does not fit the device).  Nothing else is
+ * kept: the caller picks a candidate and passes it in dock_params.
+ *   DOCK_TUNE_LS_THREADS: the local search of dock() for ligs[0] (the
+ *     paper's threads-per-block knob, Section V-B): params->nruns *
+ *     ls_count chains (ls_method's search) of min(ls_iters, 50) iterations
+ *     from an initial population; cand = threads per chain (32, 64, 128, 256).
+ *   DOCK_TUNE_BATCH_WARPS: dock_batch over ligs[0..n_ligs-1] at params
+ *     (give it a small max_evals); cand = warps per block (1, 2, 4).
+ * Errors: unknown `what`, an invalid candidate value, n_cand < 1, reps < 1. */
+#define DOCK_TUNE_LS_THREADS 1
+#define DOCK_TUNE_BATCH_WARPS 2
+int dock_tune(dock_ctx *ctx, const dock_grids *grids, const dock_ligand *const *ligs, int n_ligs,
+              const dock_params *params, int what, const int *cand, int n_cand, int reps, double *ms);
 
 /* ---- serving: continuous batching of docking requests ----
  * A server keeps a persistent docking kernel fed from a queue: each request

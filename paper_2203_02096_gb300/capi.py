@@ -37,7 +37,7 @@ class DockParams(C.Structure):
     _fields_ = [("pop_size", _i), ("nruns", _i), ("max_evals", _i64), ("ls_count", _i), ("ls_iters", _i),
                 ("rho", _f), ("eps", _f), ("p_tour", _f), ("p_cross", _f), ("p_mut", _f), ("trans_mut", _f),
                 ("ls_threads", _i), ("ls_method", _i), ("sw_rho0", _f), ("sw_rho_lo", _f), ("sw_expand", _f),
-                ("sw_contract", _f), ("sw_succ", _i), ("sw_fail", _i), ("sw_step", _f * 3)]
+                ("sw_contract", _f), ("sw_succ", _i), ("sw_fail", _i), ("sw_step", _f * 3), ("batch_warps", _i)]
 
 
 ALLOC_FN = C.CFUNCTYPE(_vp, _sz, _vp, _vp)
@@ -79,6 +79,7 @@ SIGNATURES = {
     "dock_ls_picks": (_i, [_vp, _i, _i, _i, _u64, _u32, _vp, _vp]),
     "dock_local_search": (_i, [_vp, _vp, _vp, _vp, _i, _i, _f, _f, _i, _vp, _vp, _vp]),
     "dock_philox": (_i, [_vp, _vp, _i, _u32, _u32, _vp, _vp]),
+    "dock_tune": (_i, [_vp, _vp, _vp, _i, _P(DockParams), _i, _vp, _i, _i, _vp]),
     "dock_solis_wets": (_i, [_vp, _vp, _vp, _vp, _vp, _i, _P(DockParams), _u64, _u32, _u32, _vp, _vp, _vp, _vp]),
     "dock_set_timing": (_i, [_vp, _i]),
     "dock_kernel_time": (_i, [_vp, C.c_char_p, _P(_d), _P(_i64)]),
@@ -459,6 +460,20 @@ def dock_solis_wets(ctx, grids, lig, x0: torch.Tensor, params: DockParams, E0: t
                                       C.byref(params), int(seed), int(run), int(generation), _ptr(xb), _ptr(Eb),
                                       _ptr(ev), _stream(stream)), "dock_solis_wets")
     return xb, Eb, ev
+
+
+TUNE_LS_THREADS = 1
+TUNE_BATCH_WARPS = 2
+
+
+def dock_tune(ctx, grids, ligs, params: DockParams, what: int, cand, reps: int = 3) -> np.ndarray:
+    """Mean device milliseconds per launch of each candidate shape (-1: does not fit)."""
+    cand = np.ascontiguousarray(cand, dtype=np.int32)
+    ms = np.zeros(len(cand), dtype=np.float64)
+    arr = (C.c_void_p * len(ligs))(*[l.h for l in ligs])
+    ctx.check(ctx.lib.dock_tune(ctx.h, grids.h, arr, len(ligs), C.byref(params), int(what), _ptr(cand), len(cand),
+                                int(reps), _ptr(ms)), "dock_tune")
+    return ms
 
 
 def dock_philox(ctx, ctr: torch.Tensor, key_lo: int, key_hi: int, stream=None) -> torch.Tensor:

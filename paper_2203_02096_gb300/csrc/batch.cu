@@ -271,8 +271,12 @@ extern "C" int dock_batch(dock_ctx *ctx, const dock_grids *grids, const dock_lig
         for (int r = 0; r < R; ++r) tasks.push_back(Task{k, r, k * R + r, seeds ? seeds[k] : (unsigned long long)k});
     const int gmax = 7 + DOCK_MAX_TORSIONS;
     const size_t floats_per_warp = ((2 * (size_t)P.pop_size * gmax + 3 * (size_t)P.pop_size + 63) / 64) * 64;
-    // warps per block by shared-memory fit; blocks to fill every SM
-    int wpb = 4;
+    // warps per block: as asked, else by shared-memory fit; blocks to fill every SM
+    if (P.batch_warps != 0 && P.batch_warps != 1 && P.batch_warps != 2 && P.batch_warps != 4)
+        return set_err(ctx, DOCK_ERR_INVALID, "batch_warps must be 0, 1, 2 or 4");
+    int wpb = P.batch_warps ? P.batch_warps : 4;
+    if (P.batch_warps && smem_per_warp * 4 * wpb > ctx->smem_optin)
+        return set_err(ctx, DOCK_ERR_SIZE, "batch_warps: the block's shared memory does not fit");
     while (wpb > 1 && smem_per_warp * 4 * wpb > ctx->smem_optin) wpb >>= 1;
     const size_t smem = smem_per_warp * 4 * wpb;
     auto kern = P.ls_method == 1 ? lga_persistent<1> : lga_persistent<0>;
@@ -667,3 +671,36 @@ int server_destroy(dock_server *S) {
 }
 
 }  // extern "C"
+
+// Device time of dock_batch at warps-per-block `wpb` (autotuning): reps
+// calls after one untimed call, outputs into scratch.
+int tune_batch_launch(dock_ctx *ctx, const dock_grids *grids, const dock_ligand *const *ligs, int n_ligs,
+                      const dock_params &P0, int wpb, int reps, double *ms) {
+    dock_params P = P0;
+    P.batch_warps = wpb;
+    const size_t rows = (size_t)n_ligs * P.nruns;
+    const int gmax = 7 + DOCK_MAX_TORSIONS;
+    cudaStream_t s = nullptr;
+    float *g = (float *)dev_alloc(ctx, rows * gmax * 4, s);
+    double *E = (double *)dev_alloc(ctx, rows * 8, s);
+    int rc = DOCK_OK;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (!g || !E) rc = set_err(ctx, DOCK_ERR_OOM, "dock_tune: allocation failed");
+    if (!rc && (cudaEventCreate(&e0) || cudaEventCreate(&e1))) rc = cuda_err(ctx, cudaGetLastError(), "dock_tune events");
+    if (!rc) rc = dock_batch(ctx, grids, ligs, n_ligs, &P, nullptr, g, nullptr, E, nullptr, s);
+    if (!rc) {
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < reps && !rc; ++r) rc = dock_batch(ctx, grids, ligs, n_ligs, &P, nullptr, g, nullptr, E, nullptr, s);
+        cudaEventRecord(e1, s);
+        float t = 0.f;
+        cudaError_t e = cudaEventSynchronize(e1);
+        if (!e) e = cudaEventElapsedTime(&t, e0, e1);
+        if (!rc && e) rc = cuda_err(ctx, e, "dock_tune timing");
+        if (!rc) *ms = t / reps;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    dev_free(ctx, g, s);
+    dev_free(ctx, E, s);
+    return rc;
+}

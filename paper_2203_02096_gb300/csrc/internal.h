@@ -85,12 +85,12 @@ __host__ __device__ inline int round4(int v) { return (v + 3) & ~3; }
 __host__ __device__ inline EvalLayout eval_layout(int n_atoms, int n_frag, int nb8, bool grad, int W) {
     EvalLayout w;
     int o = 0;
-    w.geno = o; o += 48;
+    w.geno = o; o += 48 * W;          // a copy per warp
     w.grad = o; o += 48;
-    w.red = o; o += 32;
-    w.M = o; o += 12 * n_frag;
+    w.red = o; o += 32;               // two halves of 8 warp partials
+    w.M = o; o += 12 * n_frag * W;    // a copy per warp
     w.fs = o; o += grad ? 8 * n_frag : 0;
-    w.x = o; o += 4 * nb8;
+    w.x = o; o += 4 * nb8 * W;        // a copy per warp
     w.f = o; o += grad ? 4 * nb8 : 0;
     w.tq = o; o += grad ? 4 * n_atoms : 0;
     w.pf = o; o += (grad && W > 1) ? 4 * 4 * W * nb8 : 0;  // W = 1 adds straight into f
@@ -146,7 +146,9 @@ void *dev_alloc(dock_ctx *ctx, size_t bytes, cudaStream_t s);
 void dev_free(dock_ctx *ctx, void *p, cudaStream_t s);
 int kernel_id(dock_ctx *ctx, const char *name);
 long long *host_status(dock_ctx *ctx);
-int check_sw(dock_ctx *ctx, const dock_params &p);  // ls_method and Solis-Wets constants  // 2 pinned words, allocated on first use; NULL on failure
+int check_sw(dock_ctx *ctx, const dock_params &p);  // ls_method and Solis-Wets constants
+int tune_batch_launch(dock_ctx *ctx, const dock_grids *grids, const dock_ligand *const *ligs, int n_ligs,
+                      const dock_params &P, int wpb, int reps, double *ms);  // 2 pinned words, allocated on first use; NULL on failure
 void timing_begin(dock_ctx *ctx, int kid, cudaStream_t s, TimedLaunch *tl);
 void timing_end(dock_ctx *ctx, cudaStream_t s, TimedLaunch *tl);
 int check_maps(dock_ctx *ctx, const dock_grids *g, const dock_ligand *l);

@@ -676,6 +676,120 @@ int dock_philox(dock_ctx *ctx, const uint32_t *ctr, int n, uint32_t key_lo, uint
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
+// Autotuning: device time of the local-search launch of dock() at a given
+// team width, from the start points of an initial population.
+
+int tune_ls_launch(dock_ctx *ctx, const dock_grids *grids, const dock_ligand *lig, const dock_params &P0,
+                   int threads, int reps, double *ms) {
+    *ms = -1.0;
+    dock_params P;
+    int rc = resolve_params(ctx, &P0, P);
+    if (rc) return rc;
+    if ((rc = check_maps(ctx, grids, lig))) return rc;
+    const LigandDev &L = lig->dev;
+    int chains = P.nruns * P.ls_count;
+    if (chains <= 0 || P.ls_iters <= 0) {
+        *ms = 0.0;
+        return DOCK_OK;
+    }
+    const int W = ls_team_warps(ctx, chains, threads, L);
+    if (32 * W != threads) return DOCK_OK;  // does not fit shared memory
+    const bool sw = P.ls_method == 1;
+    EvalLayout Y = eval_layout(L.n_atoms, L.n_frag, L.nb8, !sw, W);
+    EvalLayout Wn = eval_layout(L.n_atoms, L.n_frag, L.nb8, false, 1);
+    if (!evaluator_smem_ok(ctx, Y, 1)) return DOCK_OK;
+    const int Gn = L.n_genes;
+    int iters = std::min(P.ls_iters, 50);
+    cudaStream_t s = nullptr;
+    float *x = (float *)dev_alloc(ctx, (size_t)chains * Gn * 4, s);
+    float *xo = (float *)dev_alloc(ctx, (size_t)chains * Gn * 4, s);
+    float *E0 = (float *)dev_alloc(ctx, (size_t)chains * 4, s);
+    float *Eo = (float *)dev_alloc(ctx, (size_t)chains * 4, s);
+    unsigned long long *cnt = (unsigned long long *)dev_alloc(ctx, 8, s);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (!x || !xo || !E0 || !Eo || !cnt) {
+        rc = set_err(ctx, DOCK_ERR_OOM, "dock_tune: allocation failed");
+    } else {
+        dock_params Q = P;
+        Q.pop_size = chains;
+        GaConst C = ga_const(Q, L.n_tors, 1, 0x7475u);
+        LigandDev l = L;
+        GridDev g = grids->dev;
+        void *a[] = {&l, &g, &C, &x, &E0, &cnt, &Wn};
+        e = launch_items(ctx, init_kernel<true>, chains, 1, (size_t)Wn.total * 4, s, "tune_init", a);
+        float *no_pop = nullptr;
+        const int *no_picks = nullptr, *no_active = nullptr;
+        unsigned long long *no_ev = nullptr;
+        long long *no_eo = nullptr;
+        int zero = 0, one = 1;
+        float rho = P.rho, eps = P.eps;
+        SwConst S = sw_const(P);
+        uint2 key = make_uint2(1u, 2u);
+        uint32_t run0 = 0, gen0 = 0;
+        const float *e0p = E0;
+        void *la[] = {&l, &g, &x, &no_pop, &no_picks, &zero, &one, &chains, &iters, &rho, &eps, &xo, &Eo, &no_ev, &Y};
+        void *sa[] = {&l, &g, &x, &no_pop, &no_picks, &zero, &one, &chains, &iters, &S, &key, &run0, &gen0, &e0p,
+                      &xo, &Eo, &no_ev, &no_eo, &no_active, &Y};
+        auto one_launch = [&]() {
+            return sw ? launch_sw(ctx, W, chains, Y, s, "tune_ls", sa) : launch_ls(ctx, W, chains, Y, s, "tune_ls", la);
+        };
+        if (!e) e = one_launch();
+        if (!e) e = cudaEventCreate(&e0);
+        if (!e) e = cudaEventCreate(&e1);
+        if (!e) e = cudaEventRecord(e0, s);
+        for (int r = 0; r < reps && !e; ++r) e = one_launch();
+        if (!e) e = cudaEventRecord(e1, s);
+        if (!e) e = cudaEventSynchronize(e1);
+        float t = 0.f;
+        if (!e) e = cudaEventElapsedTime(&t, e0, e1);
+        if (e) rc = cuda_err(ctx, e, "dock_tune local search");
+        else *ms = (double)t / reps;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    dev_free(ctx, x, s);
+    dev_free(ctx, xo, s);
+    dev_free(ctx, E0, s);
+    dev_free(ctx, Eo, s);
+    dev_free(ctx, cnt, s);
+    return rc;
+}
+
+extern "C" int dock_tune(dock_ctx *ctx, const dock_grids *grids, const dock_ligand *const *ligs, int n_ligs,
+                         const dock_params *params, int what, const int *cand, int n_cand, int reps, double *ms) {
+    if (!ctx) return DOCK_ERR_INVALID;
+    if (!grids || !ligs || n_ligs < 1 || !cand || n_cand < 1 || reps < 1 || !ms)
+        return set_err(ctx, DOCK_ERR_INVALID, "dock_tune: invalid argument");
+    for (int k = 0; k < n_ligs; ++k)
+        if (!ligs[k]) return set_err(ctx, DOCK_ERR_INVALID, "dock_tune: null ligand");
+    dock_params P;
+    if (params) P = *params;
+    else dock_default_params(&P);
+    for (int i = 0; i < n_cand; ++i) {
+        const int c = cand[i];
+        int rc = DOCK_OK;
+        if (what == DOCK_TUNE_LS_THREADS) {
+            if (c != 32 && c != 64 && c != 128 && c != 256)
+                return set_err(ctx, DOCK_ERR_INVALID, "dock_tune: threads must be 32, 64, 128 or 256");
+            rc = tune_ls_launch(ctx, grids, ligs[0], P, c, reps, &ms[i]);
+        } else if (what == DOCK_TUNE_BATCH_WARPS) {
+            if (c != 1 && c != 2 && c != 4) return set_err(ctx, DOCK_ERR_INVALID, "dock_tune: warps must be 1, 2 or 4");
+            ms[i] = -1.0;
+            rc = tune_batch_launch(ctx, grids, ligs, n_ligs, P, c, reps, &ms[i]);
+            if (rc == DOCK_ERR_SIZE) {  // this width does not fit: reported as -1
+                ms[i] = -1.0;
+                rc = DOCK_OK;
+            }
+        } else {
+            return set_err(ctx, DOCK_ERR_INVALID, "dock_tune: unknown kernel family");
+        }
+        if (rc) return rc;
+    }
+    return DOCK_OK;
+}
+
+// ---------------------------------------------------------------------------
 // dock_async_noalloc: the docking of dock_async with its working buffers
 // (two populations, their energies, the local-search picks and the per-run
 // evaluation counters) carved out of one fixed device array instead of

@@ -1,0 +1,61 @@
+"""Autotuning on the GPU: dock_tune times every candidate width of the
+local search and of the batch kernel; a tuned docking is the docking at the
+chosen width; the batch kernel's warps per block never change a result."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2203_02096_gb300 import autotune, capi, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def test_ls_widths_timed_and_tuned_docking_reproducible(gpu, drug_system, tmp_path):
+    L = capi.ligand_from(gpu, drug_system["lig"])
+    G = capi.grids_from_maps(gpu, drug_system["maps"], drug_system["box"])
+    P = capi.default_params(nruns=20, max_evals=20_000, ls_iters=60)
+    curve = autotune.ls_curve(gpu, G, L, P)
+    assert all(v["ms"] > 0 for v in curve.values()), curve
+    t = autotune.Tuner(gpu, path=str(tmp_path / "tune.json"))
+    Pt = t.tuned(G, L, P)
+    assert Pt.ls_threads in autotune.LS_CANDIDATES
+    assert t.tuned(G, L, P).ls_threads == Pt.ls_threads          # cached
+    a = capi.dock(gpu, G, L, Pt, 3)
+    P2 = capi.default_params(nruns=20, max_evals=20_000, ls_iters=60, ls_threads=Pt.ls_threads)
+    b = capi.dock(gpu, G, L, P2, 3)
+    assert all(np.array_equal(x, y) for x, y in zip(a, b))
+    # the Solis-Wets search is timed too
+    Ps = capi.default_params(nruns=20, max_evals=20_000, ls_iters=60, ls_method=1)
+    assert all(v["ms"] > 0 for v in autotune.ls_curve(gpu, G, L, Ps).values())
+
+
+def test_batch_warps_do_not_change_results(gpu, drug_system, tmp_path):
+    rng = np.random.default_rng(2)
+    ligs = [synth.make_ligand(int(rng.integers(10, 109)), int(rng.integers(0, 33)), seed=500 + k) for k in range(9)]
+    L = [capi.ligand_from(gpu, l) for l in ligs]
+    G = capi.grids_from_maps(gpu, drug_system["maps"], drug_system["box"])
+    outs = []
+    for w in (1, 2, 4):
+        P = capi.default_params(pop_size=30, nruns=2, max_evals=1500, ls_iters=10, batch_warps=w)
+        outs.append(capi.dock_batch(gpu, G, L, P, np.arange(9, dtype=np.uint64)))
+    torch.cuda.synchronize()
+    for o in outs[1:]:
+        for k in ("best_geno", "best_E", "evals"):
+            assert torch.equal(o[k], outs[0][k]), k
+    t = autotune.Tuner(gpu, path=str(tmp_path / "tune.json"))
+    P = capi.default_params(pop_size=30, nruns=2, max_evals=1500, ls_iters=10)
+    assert t.tuned(G, L, P).batch_warps in autotune.BATCH_CANDIDATES
+    ms = capi.dock_tune(gpu, G, L, P, capi.TUNE_BATCH_WARPS, [1, 2, 4], 1)
+    assert np.all(ms > 0)
+
+
+def test_tune_rejects_bad_requests(gpu, drug_system):
+    L = capi.ligand_from(gpu, drug_system["lig"])
+    G = capi.grids_from_maps(gpu, drug_system["maps"], drug_system["box"])
+    P = capi.default_params(nruns=2)
+    with pytest.raises(capi.DockError):
+        capi.dock_tune(gpu, G, [L], P, 99, [32])
+    with pytest.raises(capi.DockError):
+        capi.dock_tune(gpu, G, [L], P, capi.TUNE_LS_THREADS, [48])
+    with pytest.raises(capi.DockError):
+        capi.dock_batch(gpu, G, [L], capi.default_params(nruns=2, batch_warps=3))
