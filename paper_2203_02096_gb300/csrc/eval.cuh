@@ -25,9 +25,11 @@ namespace dev {
 constexpr float kDielA = -8.5525f;
 constexpr float kDielB = (float)(78.4 + 8.5525);
 constexpr float kDielK = 7.7839f;
-constexpr float kDielLB = (float)(0.003627 * (78.4 + 8.5525));
+// exponents in base 2: e^{-a x} = 2^{-a log2(e) x}
+constexpr double kLog2e = 1.4426950408889634;
+constexpr float kDielLB2 = (float)(0.003627 * (78.4 + 8.5525) * kLog2e);
 constexpr float kDielDeps = (float)((78.4 + 8.5525) * 7.7839 * 0.003627 * (78.4 + 8.5525));
-constexpr float kHalfInvSig2 = (float)(1.0 / (2.0 * 3.6 * 3.6));
+constexpr float kHalfInvSig2L2 = (float)(kLog2e / (2.0 * 3.6 * 3.6));
 constexpr float kInvSig2 = (float)(1.0 / (3.6 * 3.6));
 constexpr float kCut2 = 64.0f;
 constexpr float kFloor2 = 0.25f;
@@ -35,6 +37,19 @@ constexpr float kKout = 10.0f;
 
 template <typename T>
 __device__ __forceinline__ T ldg(const T *p) { return __ldg(p); }
+
+// 2^x and 1/x by the special-function unit (ex2.approx / rcp.approx, about
+// 2 ulp; inputs far below 0 give 0).
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 
 // W warps evaluating one genotype.  W = 1: a warp, possibly one of several
 // independent teams in a block; W > 1: the whole block is the team.
@@ -161,19 +176,20 @@ __device__ __forceinline__ float pair_energy(float r2, float4 c, float &s) {
     const float rk = hb ? ri6 * ri2 * ri2 : ri6;  // r^-10 or r^-6
     const float cn = fabsf(c.y);
     const float ev = fmaf(c.x, ri12, -cn * rk);
-    // sigmoidal dielectric eps = A + B / (1 + k exp(-lambda B r))
-    const float ex = __expf(-kDielLB * r);
-    const float inv_den = __fdividef(1.f, fmaf(kDielK, ex, 1.f));
-    const float eps = fmaf(kDielB, inv_den, kDielA);
-    const float inv_eps = __fdividef(1.f, eps);
+    // sigmoidal dielectric eps = A + B / den, den = 1 + k exp(-lambda B r):
+    // eps = D / den with D = A den + B, so one reciprocal rr = 1 / (den D)
+    // gives 1/eps = den^2 rr and eps'/eps = B k lambda B e rr
+    const float ex = ex2_approx(-kDielLB2 * r);
+    const float den = fmaf(kDielK, ex, 1.f);
+    const float rr = rcp_approx(den * fmaf(kDielA, den, kDielB));
+    const float inv_eps = (den * den) * rr;
     // products rounded on their own (never fused into the sum below), so the
     // energy has the same bits with and without the gradient
     const float eel = __fmul_rn(__fmul_rn(c.z, rinv), inv_eps);
-    const float eds = __fmul_rn(c.w, __expf(-r2e * kHalfInvSig2));
+    const float eds = __fmul_rn(c.w, ex2_approx(-r2e * kHalfInvSig2L2));
     if (GRAD) {
         const float dv = fmaf(-12.f * c.x, ri12, (hb ? 10.f : 6.f) * cn * rk) * rinv;
-        // eps' / eps with eps' = B k lambda B e / (1 + k e)^2
-        const float deps_eps = kDielDeps * ex * inv_den * inv_den * inv_eps;
+        const float deps_eps = kDielDeps * ex * rr;
         const float del = -eel * (rinv + deps_eps);  // d(qq / (eps r)) / dr
         const float dds = -eds * r * kInvSig2;
         s = r2 >= kFloor2 ? (dv + del + dds) * rinv : 0.f;
@@ -351,37 +367,53 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
         const int nxt = gb | ((sl + 1) & 7);
         float4 *pq = W == 1 ? Fv : PF + q * NB;  // W = 1: the step's groups touch disjoint atoms
         const int s0 = SD.base[w], s1 = s0 + SD.steps[w];
+        // one round: the pair (own atom, atom 8B + (sl + d) mod 8) with
+        // coefficients c; the force owed to the B atom travels one lane on
+        auto round = [&](const float4 &xa, int B, int d, const float4 &c, float &ax, float &ay, float &az, float &bx,
+                         float &by, float &bz) {
+            const float4 xb = X[8 * B + ((sl + d) & 7)];
+            const float ddx = xa.x - xb.x, ddy = xa.y - xb.y, ddz = xa.z - xb.z;
+            const float r2 = fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz));
+            // every round computes; the cutoff selects (one basic block for
+            // all rounds, so they overlap)
+            float s;
+            const float ep = pair_energy<GRAD>(r2, c, s);
+            const bool in = r2 < kCut2;
+            e += in ? ep : 0.f;
+            if (GRAD) {
+                s = in ? s : 0.f;
+                const float fx = s * ddx, fy = s * ddy, fz = s * ddz;
+                ax += fx; ay += fy; az += fz;
+                bx = __shfl_sync(0xffffffffu, bx - fx, nxt);
+                by = __shfl_sync(0xffffffffu, by - fy, nxt);
+                bz = __shfl_sync(0xffffffffu, bz - fz, nxt);
+            }
+        };
         for (int st = s0; st < s1; ++st) {
             const uint32_t ctl = ldg(SD.ctrl + 4 * st + (lane >> 3));
             const int A = SCH_A(ctl), B = SCH_B(ctl);
             const float4 xa = X[8 * A + sl];
             const float4 *rp = SD.rec + 256 * (size_t)st + lane;
             float ax = 0.f, ay = 0.f, az = 0.f, bx = 0.f, by = 0.f, bz = 0.f;
+            if (W == 1 && (ctl & SCH_HALF)) {
+                // diagonal blocks, rounds 1-4: the travelling force ends 4
+                // lanes on; the atom's owner fetches it from lane sl + 3
 #pragma unroll
-            for (int d = 0; d < 8; ++d) {
-                const float4 c = ldg(rp + 32 * d);
-                const float4 xb = X[8 * B + ((sl + d) & 7)];
-                const float ddx = xa.x - xb.x, ddy = xa.y - xb.y, ddz = xa.z - xb.z;
-                const float r2 = fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz));
-                // every round computes; the cutoff selects (one basic block for
-                // all 8 rounds, so they overlap)
-                float s;
-                const float ep = pair_energy<GRAD>(r2, c, s);
-                const bool in = r2 < kCut2;
-                e += in ? ep : 0.f;
+                for (int d = 1; d <= 4; ++d) round(xa, B, d, ldg(rp + 32 * d), ax, ay, az, bx, by, bz);
                 if (GRAD) {
-                    s = in ? s : 0.f;
-                    const float fx = s * ddx, fy = s * ddy, fz = s * ddz;
-                    ax += fx; ay += fy; az += fz;
-                    bx = __shfl_sync(0xffffffffu, bx - fx, nxt);
-                    by = __shfl_sync(0xffffffffu, by - fy, nxt);
-                    bz = __shfl_sync(0xffffffffu, bz - fz, nxt);
+                    const int src = gb | ((sl + 3) & 7);
+                    bx = __shfl_sync(0xffffffffu, bx, src);
+                    by = __shfl_sync(0xffffffffu, by, src);
+                    bz = __shfl_sync(0xffffffffu, bz, src);
                 }
+            } else {
+#pragma unroll
+                for (int d = 0; d < 8; ++d) round(xa, B, d, ldg(rp + 32 * d), ax, ay, az, bx, by, bz);
             }
             if (GRAD && (ctl & SCH_VALID)) {
                 float4 pa = pq[8 * A + sl];
                 pa.x += ax; pa.y += ay; pa.z += az;
-                pq[8 * A + sl] = pa;
+                pq[8 * A + sl] = pa;  // (a diagonal block's second update below is this thread's too)
                 float4 pb = pq[8 * B + sl];
                 pb.x += bx; pb.y += by; pb.z += bz;
                 pq[8 * B + sl] = pb;

@@ -388,78 +388,92 @@ struct Blob {
     }
 };
 
-// Systolic pair schedule for a team of W warps (see SchedDev): one step per
-// block pair holding at least one listed pair.  W = 1: steps are matchings
-// (the warp's 4 groups touch disjoint blocks), so the warp can add pair forces
-// straight into per-atom forces; W > 1: block pairs dealt round-robin to the
-// 4W groups, each with its own partial forces.  Each warp runs as many steps
+// Systolic pair schedule for a team of W warps (see SchedDev): every block
+// pair holding at least one listed pair is one group-step.  W = 1: steps are
+// matchings (the warp's 4 groups touch disjoint blocks), so the warp can add
+// pair forces straight into per-atom forces.  Off-diagonal block pairs are
+// packed 4 to a step in the order of a round-robin tournament (circle
+// method), diagonal blocks fill free groups of those steps (8 rounds, half
+// coefficients: each pair is met twice), and the remaining diagonal blocks
+// go 4 to a half step of 4 rounds (rounds 1-3 meet each pair once, round 4
+// twice at half coefficients).  W > 1: block pairs dealt round-robin to the
+// 4W groups, each with its own partial forces; each warp runs as many steps
 // as its busiest group.
 struct SchedHost {
     std::vector<uint32_t> ctrl;
     std::vector<float4> rec;
     int base[8] = {0}, steps[8] = {0};
-    double listed = 0;  // pair slots weighted 1 (0.5 on diagonal steps); must equal the pair count
+    double listed = 0;  // pair slots weighted by how often a step meets them; must equal the pair count
 };
 
 SchedHost build_sched(int n, int W, const std::vector<int> &pidx, const std::vector<float4> &pc) {
     const int nb = (n + 7) / 8, NG = 4 * W;
+    auto nonempty = [&](int A, int B) {
+        for (int a = 8 * A; a < 8 * A + 8 && a < n; ++a)
+            for (int b = (A == B ? a + 1 : 8 * B); b < 8 * B + 8 && b < n; ++b)
+                if (pidx[(size_t)a * n + b] >= 0) return true;
+        return false;
+    };
     std::vector<std::pair<int, int>> bps;
-    for (int A = 0; A < nb; ++A)
-        for (int B = A; B < nb; ++B) {
-            bool any = false;
-            for (int a = 8 * A; a < 8 * A + 8 && a < n && !any; ++a)
-                for (int b = (A == B ? a + 1 : 8 * B); b < 8 * B + 8 && b < n && !any; ++b)
-                    any = pidx[(size_t)a * n + b] >= 0;
-            if (any) bps.push_back({A, B});
-        }
-    std::vector<std::vector<int>> glist(NG);
+    std::vector<std::vector<int>> glist(NG);  // per group: block-pair index per step, -1 idle
+    std::vector<char> half;                   // W = 1: per step, a half (diagonal) step
     if (W == 1) {
-        // one warp accumulates straight into per-atom forces: the 4 block pairs
-        // of a step must touch disjoint blocks.  Order the block pairs by the
-        // rounds of a round-robin tournament over the blocks (circle method:
-        // each round is a perfect matching; a block paired with the padding
-        // block gets its diagonal pair), then pack greedily, 4 per step.
-        {
-            const int ne = nb + (nb & 1);
-            std::vector<std::pair<int, int>> order;
-            std::vector<char> diag_done(nb, 0);
-            for (int rr = 0; rr < ne - 1; ++rr) {
-                std::vector<int> arr(ne);
-                arr[0] = ne - 1;
-                for (int i = 1; i < ne; ++i) arr[i] = (rr + i - 1) % (ne - 1);
-                for (int i = 0; i < ne / 2; ++i) {
-                    int a = arr[i], b = arr[ne - 1 - i];
-                    if (a > b) std::swap(a, b);
-                    if (b >= nb) {
-                        order.push_back({a, a});
-                        diag_done[a] = 1;
-                    } else {
-                        order.push_back({a, b});
-                    }
-                }
+        // off-diagonal pairs in circle-method order
+        const int ne = nb + (nb & 1);
+        for (int rr = 0; rr < ne - 1; ++rr) {
+            std::vector<int> arr(ne);
+            arr[0] = ne - 1;
+            for (int i = 1; i < ne; ++i) arr[i] = (rr + i - 1) % (ne - 1);
+            for (int i = 0; i < ne / 2; ++i) {
+                int a = arr[i], b = arr[ne - 1 - i];
+                if (a > b) std::swap(a, b);
+                if (b < nb && nonempty(a, b)) bps.push_back({a, b});
             }
-            for (int d = 0; d < nb; ++d)
-                if (!diag_done[d]) order.push_back({d, d});
-            std::vector<std::pair<int, int>> keep;
-            for (const auto &e : order)
-                if (std::find(bps.begin(), bps.end(), e) != bps.end()) keep.push_back(e);
-            bps = keep;
         }
-        std::vector<char> done(bps.size(), 0);
-        size_t left = bps.size();
+        const size_t n_off = bps.size();
+        std::vector<int> diag;
+        for (int d = 0; d < nb; ++d)
+            if (nonempty(d, d)) diag.push_back(d);
+        std::vector<char> done(n_off, 0), dused(diag.size(), 0);
+        size_t left = n_off;
         while (left) {
             std::vector<char> used(nb, 0);
             int q = 0;
-            for (size_t i = 0; i < bps.size() && q < 4; ++i) {
+            for (size_t i = 0; i < n_off && q < 4; ++i) {
                 if (done[i] || used[bps[i].first] || used[bps[i].second]) continue;
                 used[bps[i].first] = used[bps[i].second] = 1;
                 done[i] = 1;
                 --left;
                 glist[q++].push_back((int)i);
             }
-            for (; q < 4; ++q) glist[q].push_back(-1);  // idle group this step
+            for (size_t k = 0; k < diag.size() && q < 4; ++k) {  // free groups take diagonal blocks
+                if (dused[k] || used[diag[k]]) continue;
+                used[diag[k]] = 1;
+                dused[k] = 1;
+                bps.push_back({diag[k], diag[k]});
+                glist[q++].push_back((int)bps.size() - 1);
+            }
+            for (; q < 4; ++q) glist[q].push_back(-1);
+            half.push_back(0);
+        }
+        int q = 0;
+        for (size_t k = 0; k < diag.size(); ++k) {
+            if (dused[k]) continue;
+            bps.push_back({diag[k], diag[k]});
+            glist[q++].push_back((int)bps.size() - 1);
+            if (q == 4) {
+                half.push_back(1);
+                q = 0;
+            }
+        }
+        if (q) {
+            for (; q < 4; ++q) glist[q].push_back(-1);
+            half.push_back(1);
         }
     } else {
+        for (int A = 0; A < nb; ++A)
+            for (int B = A; B < nb; ++B)
+                if (nonempty(A, B)) bps.push_back({A, B});
         for (size_t i = 0; i < bps.size(); ++i) glist[i % NG].push_back((int)i);
     }
     SchedHost S;
@@ -478,15 +492,17 @@ SchedHost build_sched(int n, int W, const std::vector<int> &pidx, const std::vec
     for (int w = 0; w < W; ++w)
         for (int q = 0; q < 4; ++q) {
             int st = S.base[w];
-            for (int bi : glist[4 * w + q]) {
+            for (size_t k = 0; k < glist[4 * w + q].size(); ++k, ++st) {
+                const bool hs = W == 1 && half[k];
+                const int bi = glist[4 * w + q][k];
                 if (bi < 0) {  // idle: valid flag clear, zero records
-                    ++st;
+                    S.ctrl[4 * (size_t)st + q] = hs ? SCH_HALF : 0u;
                     continue;
                 }
                 const int A = bps[bi].first, B = bps[bi].second;
                 const bool diag = A == B;
-                S.ctrl[4 * (size_t)st + q] = (uint32_t)A | ((uint32_t)B << 5) | SCH_VALID;
-                for (int d = 0; d < 8; ++d)
+                S.ctrl[4 * (size_t)st + q] = (uint32_t)A | ((uint32_t)B << 5) | SCH_VALID | (hs ? SCH_HALF : 0u);
+                for (int d = hs ? 1 : 0; d < (hs ? 5 : 8); ++d)
                     for (int sl = 0; sl < 8; ++sl) {
                         const int a = 8 * A + sl, b = 8 * B + ((sl + d) & 7);
                         if (a >= n || b >= n || a == b) continue;
@@ -495,13 +511,14 @@ SchedHost build_sched(int n, int W, const std::vector<int> &pidx, const std::vec
                         if (pp < 0) continue;
                         const size_t o = 256 * (size_t)st + 32 * d + 8 * q + sl;
                         float4 c = pc[pp];
-                        if (diag) {  // met twice: half each time (exact in FP32)
+                        // met twice in the step: half each time (exact in FP32)
+                        const bool twice = diag && (!hs || d == 4);
+                        if (twice) {
                             c.x *= 0.5f; c.y *= 0.5f; c.z *= 0.5f; c.w *= 0.5f;
                         }
                         S.rec[o] = c;
-                        S.listed += diag ? 0.5 : 1.0;
+                        S.listed += twice ? 0.5 : 1.0;
                     }
-                ++st;
             }
         }
     return S;

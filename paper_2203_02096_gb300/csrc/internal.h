@@ -20,8 +20,10 @@
 // Atoms form blocks of 8; a step is one block pair (A, B), 8 rounds: in
 // round d lane l of the group pairs atom 8A + l with atom 8B + (l + d) mod 8.
 // A diagonal step (A == B) meets every pair of its block twice (rounds d and
-// 8 - d), each time with half the coefficients.  ctrl[step][group of the
-// warp] packs A, B and a valid flag; rec[step][round][lane] holds the pair
+// 8 - d), each time with half the coefficients; a half step (one-warp teams,
+// every group diagonal) runs rounds 1-4 only, round 4 at half coefficients.
+// ctrl[step][group of the warp] packs A, B, a valid flag and the half-step
+// flag (set on all four groups of a half step); rec[step][round][lane] holds the pair
 // coefficients (c12, cn, qq, ds) -- cn = c6 for 12-6 pairs, -c10 for 12-10
 // H-bond pairs -- zero for pairs outside the pair list.
 struct SchedDev {
@@ -34,6 +36,7 @@ struct SchedDev {
 #define SCH_A(c) ((c) & 31u)
 #define SCH_B(c) (((c) >> 5) & 31u)
 #define SCH_VALID 0x10000u
+#define SCH_HALF 0x20000u  // W = 1 half step: diagonal blocks, rounds 1-4 only
 
 struct LigandDev {
     int n_atoms, n_tors, n_frag, n_pairs, n_genes, max_depth;
