@@ -358,9 +358,12 @@ def score_grad_throughput(ctx, G, box, dev, reps: int = 5):
     FP32 roofline of that kernel (inputs resident, L2 flushed between calls)."""
     import torch
 
-    from paper_2203_02096_gb300 import capi, synth
+    from paper_2203_02096_gb300 import autotune, capi, synth
     lig = synth.make_ligand(64, 16, seed=0)
     L = capi.ligand_from(ctx, lig)
+    # register cap of the scorer by the autotuner (untimed)
+    tuner = autotune.Tuner(ctx, path=os.path.join(tempfile.mkdtemp(prefix="dock_tune_"), "tune.json"))
+    blocks = tuner.score_blocks(G, L)
     genos = torch.from_numpy(synth.make_genotypes(65536, lig.n_torsions, box, seed=0)).to(dev)
     E = torch.empty(65536, device=dev)
     grad = torch.empty_like(genos)
@@ -383,11 +386,28 @@ def score_grad_throughput(ctx, G, box, dev, reps: int = 5):
     f = flops_score_grad(lig.n_atoms, lig.n_torsions, len(pij), p_in)
     t = float(np.mean(ms)) / 1e3
     L.free()
+    capi.set_option(ctx, capi.OPT_SCORE_BLOCKS, 1)
     achieved = f * 65536 / t / 1e12
     return {"workload": "65536 genotypes, 64 atoms / 16 torsions, 64^3 x 9 maps", "evals_per_s": 65536 / t,
             "launch_ms": t * 1e3, "flops_per_eval": f, "achieved_tflops": achieved,
             "frac_fp32_peak": achieved / peak_fp32_tflops(),
-            "l2_achieved_gbs": grid_bytes_per_eval(lig.n_atoms) * 65536 / t / 1e9}
+            "l2_achieved_gbs": grid_bytes_per_eval(lig.n_atoms) * 65536 / t / 1e9,
+            "autotuned_score_blocks": blocks, "score_blocks_ms": tuner.curve("|score|")}
+
+
+def run_score_grad_only() -> int:
+    """The score_grad_batch measurement alone (drug-size grids built on the GPU)."""
+    import torch
+
+    from paper_2203_02096_gb300 import capi
+    dev = torch.device("cuda", 0)
+    w = workload()
+    ctx = capi.Context(0)
+    G = capi.grids_from_receptor(ctx, w.receptor, w.box)
+    print(json.dumps(score_grad_throughput(ctx, G, w.box, dev)), flush=True)
+    G.free()
+    ctx.close()
+    return 0
 
 
 def batched_docking(ctx, dev, n_ligs: int = 1024, nruns: int = 20, evals_per_run: int = 20_000,
@@ -413,6 +433,7 @@ def batched_docking(ctx, dev, n_ligs: int = 1024, nruns: int = 20, evals_per_run
     tuner = autotune.Tuner(ctx, path=os.path.join(tempfile.mkdtemp(prefix="dock_tune_"), "tune.json"))
     Pb = capi.DockParams.from_buffer_copy(P)
     Pb.batch_warps = tuner.batch_warps(G, L, P, probe_generations=1)
+    batch_blocks = tuner.batch_blocks(G, L, Pb, probe_generations=1)   # register cap, set on the context
     capi.dock_batch(ctx, G, L[:8], Pb, seeds[:8])          # warm-up
     torch.cuda.synchronize(dev)
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -434,6 +455,7 @@ def batched_docking(ctx, dev, n_ligs: int = 1024, nruns: int = 20, evals_per_run
     t_plain = time.perf_counter() - t0
     for h in L + [G]:
         h.free()
+    capi.set_option(ctx, capi.OPT_BATCH_BLOCKS, 4)
     rate_b, rate_p = ev_batch / t_batch, ev_plain / t_plain
     per_lig_full = nruns * full_budget
     return {"workload": f"{n_ligs} ligands (10-108 atoms, 0-32 torsions), {nruns} runs, pop 150, 80^3 x 9 maps",
@@ -444,6 +466,7 @@ def batched_docking(ctx, dev, n_ligs: int = 1024, nruns: int = 20, evals_per_run
             "plain_ligands_per_hour_extrapolated": 3600.0 * rate_p / per_lig_full,
             "batch_seconds": t_batch, "launches": 1,
             "autotuned": {"batch_warps": int(Pb.batch_warps), "batch_warps_ms": tuner.curve("|batch|"),
+                          "batch_blocks": int(batch_blocks), "batch_blocks_ms": tuner.curve("|batchregs|"),
                           "plain_ls_threads": [int(p.ls_threads) for p in plain_params]}}
 
 
@@ -624,7 +647,11 @@ def main(argv=None):
     ap.add_argument("--no-batch", action="store_true", help="skip the score_grad_batch side measurement")
     ap.add_argument("--ls-threads", type=int, default=-1,
                     help="threads per local-search chain (-1 = autotuned, 0 = library default)")
+    ap.add_argument("--only", choices=["score_grad"], default=None,
+                    help="run one side measurement alone and print its JSON (for profiling)")
     args = ap.parse_args(argv)
+    if args.only == "score_grad":
+        return run_score_grad_only()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":

@@ -230,11 +230,34 @@ int dock_batch(dock_ctx *ctx, const dock_grids *grids, const dock_ligand *const 
  *     from an initial population; cand = threads per chain (32, 64, 128, 256).
  *   DOCK_TUNE_BATCH_WARPS: dock_batch over ligs[0..n_ligs-1] at params
  *     (give it a small max_evals); cand = warps per block (1, 2, 4).
+ *   DOCK_TUNE_SCORE_BLOCKS: score_grad_batch of params->pop_size * nruns
+ *     genotypes of ligs[0] (an initial population); cand = the register cap
+ *     as DOCK_OPT_SCORE_BLOCKS values (1, 6, 8).  The context's own setting is
+ *     restored afterwards.
+ *   DOCK_TUNE_BATCH_BLOCKS: dock_batch as for DOCK_TUNE_BATCH_WARPS; cand =
+ *     the register cap as DOCK_OPT_BATCH_BLOCKS values (3, 4).
  * Errors: unknown `what`, an invalid candidate value, n_cand < 1, reps < 1. */
 #define DOCK_TUNE_LS_THREADS 1
 #define DOCK_TUNE_BATCH_WARPS 2
+#define DOCK_TUNE_SCORE_BLOCKS 3
+#define DOCK_TUNE_BATCH_BLOCKS 4
 int dock_tune(dock_ctx *ctx, const dock_grids *grids, const dock_ligand *const *ligs, int n_ligs,
               const dock_params *params, int what, const int *cand, int n_cand, int reps, double *ms);
+
+/* Context options.  DOCK_OPT_SCORE_BLOCKS: register cap of the batched
+ * scorers (score_batch, score_grad_batch) as the blocks of 128 threads per
+ * SM the registers must leave room for: 1 (the compiler's choice, default),
+ * 6 (<= 80 registers per thread) or 8 (<= 64).  It changes speed only, never
+ * a result (the paper's register-use tuning, Section V-B).  Errors: unknown
+ * option or value. */
+#define DOCK_OPT_SCORE_BLOCKS 1
+/* DOCK_OPT_BATCH_BLOCKS: register cap of dock_batch's and the server's
+ * persistent docking kernel, as blocks of 128 threads per SM: 4 (<= 128
+ * registers per thread, default) or 3 (<= 168; fewer spills, fewer warps).
+ * A server takes the value set when server_create is called.  Speed only. */
+#define DOCK_OPT_BATCH_BLOCKS 2
+int dock_set_option(dock_ctx *ctx, int option, int value);
+int dock_get_option(const dock_ctx *ctx, int option, int *value);
 
 /* ---- serving: continuous batching of docking requests ----
  * A server keeps a persistent docking kernel fed from a queue: each request

@@ -2,9 +2,11 @@
 
 The paper tunes threads per block and register use per GPU (Section V-B);
 here the knobs are the threads that evaluate one local-search chain of a
-docking (``dock_params.ls_threads``: 32..256, one to eight warps per chain)
-and the warps per block of the persistent batch kernel
-(``dock_params.batch_warps``).  The tuner times every candidate on the
+docking (``dock_params.ls_threads``: 32..256, one to eight warps per chain),
+the warps per block of the persistent batch kernel
+(``dock_params.batch_warps``) and the register cap of the batched scorers
+(context option ``DOCK_OPT_SCORE_BLOCKS``: 1, 6 or 8 blocks per SM) and
+of the persistent docking kernel (``DOCK_OPT_BATCH_BLOCKS``: 4 or 3).  The tuner times every candidate on the
 device through ``dock_tune`` (CUDA events inside the library, one untimed
 launch first), keeps the fastest, and caches the choice in a JSON file keyed
 by device name and workload shape, so a shape is timed once per machine.
@@ -25,6 +27,8 @@ from . import capi
 
 LS_CANDIDATES = (32, 64, 128, 256)
 BATCH_CANDIDATES = (1, 2, 4)
+SCORE_BLOCK_CANDIDATES = (1, 6, 8)
+BATCH_BLOCK_CANDIDATES = (4, 3)
 LS_PROBE_ITERS = 50          # dock_tune times at most this many iterations per chain
 
 
@@ -92,6 +96,34 @@ class Tuner:
         return self._pick(key, BATCH_CANDIDATES, lambda c: capi.dock_tune(self.ctx, grids, ligs, probe,
                                                                           capi.TUNE_BATCH_WARPS, c, 1))
 
+    def batch_blocks(self, grids: capi.Grids, ligs, params: capi.DockParams, probe_generations: int = 2,
+                     apply: bool = True) -> int:
+        """Register cap of the persistent docking kernel for this ligand set
+        (timed like batch_warps); set on the context."""
+        sizes = sorted(l.n_atoms for l in ligs)
+        key = "|".join(str(v) for v in (self.device_name, "batchregs", params.ls_method, params.pop_size, len(ligs),
+                                         params.nruns, params.batch_warps, sizes[0], sizes[len(sizes) // 2],
+                                         sizes[-1]))
+        probe = capi.DockParams.from_buffer_copy(params)
+        n_ls = params.ls_count if params.ls_count >= 0 else (6 * params.pop_size + 99) // 100
+        probe.max_evals = params.pop_size + probe_generations * ((params.pop_size - 1) + n_ls * params.ls_iters)
+        choice = self._pick(key, BATCH_BLOCK_CANDIDATES, lambda c: capi.dock_tune(self.ctx, grids, ligs, probe,
+                                                                                  capi.TUNE_BATCH_BLOCKS, c, 1))
+        if apply:
+            capi.set_option(self.ctx, capi.OPT_BATCH_BLOCKS, choice)
+        return choice
+
+    def score_blocks(self, grids: capi.Grids, lig: capi.Ligand, batch: int = 65536, apply: bool = True) -> int:
+        """Register cap of score_batch / score_grad_batch for this ligand,
+        timed on a batch of about `batch` genotypes; set on the context."""
+        key = "|".join(str(v) for v in (self.device_name, "score", lig.n_atoms, lig.n_torsions, lig.n_pairs, batch))
+        probe = capi.default_params(pop_size=1024, nruns=max(1, batch // 1024))
+        choice = self._pick(key, SCORE_BLOCK_CANDIDATES,
+                            lambda c: capi.dock_tune(self.ctx, grids, [lig], probe, capi.TUNE_SCORE_BLOCKS, c, self.reps))
+        if apply:
+            capi.set_option(self.ctx, capi.OPT_SCORE_BLOCKS, choice)
+        return choice
+
     def tuned(self, grids: capi.Grids, ligs, params: capi.DockParams) -> capi.DockParams:
         """A copy of params with ls_threads (one ligand) or batch_warps (a list) chosen."""
         p = capi.DockParams.from_buffer_copy(params)
@@ -116,4 +148,5 @@ def ls_curve(ctx, grids, lig, params, reps: int = 3) -> dict:
             for c, m in zip(LS_CANDIDATES, ms)}
 
 
-__all__ = ["Tuner", "ls_curve", "default_cache_path", "LS_CANDIDATES", "BATCH_CANDIDATES"]
+__all__ = ["Tuner", "ls_curve", "default_cache_path", "LS_CANDIDATES", "BATCH_CANDIDATES", "SCORE_BLOCK_CANDIDATES",
+           "BATCH_BLOCK_CANDIDATES"]

@@ -80,6 +80,8 @@ SIGNATURES = {
     "dock_local_search": (_i, [_vp, _vp, _vp, _vp, _i, _i, _f, _f, _i, _vp, _vp, _vp]),
     "dock_philox": (_i, [_vp, _vp, _i, _u32, _u32, _vp, _vp]),
     "dock_tune": (_i, [_vp, _vp, _vp, _i, _P(DockParams), _i, _vp, _i, _i, _vp]),
+    "dock_set_option": (_i, [_vp, _i, _i]),
+    "dock_get_option": (_i, [_vp, _i, _P(_i)]),
     "dock_solis_wets": (_i, [_vp, _vp, _vp, _vp, _vp, _i, _P(DockParams), _u64, _u32, _u32, _vp, _vp, _vp, _vp]),
     "dock_set_timing": (_i, [_vp, _i]),
     "dock_kernel_time": (_i, [_vp, C.c_char_p, _P(_d), _P(_i64)]),
@@ -464,6 +466,20 @@ def dock_solis_wets(ctx, grids, lig, x0: torch.Tensor, params: DockParams, E0: t
 
 TUNE_LS_THREADS = 1
 TUNE_BATCH_WARPS = 2
+TUNE_SCORE_BLOCKS = 3
+TUNE_BATCH_BLOCKS = 4
+OPT_SCORE_BLOCKS = 1
+OPT_BATCH_BLOCKS = 2
+
+
+def set_option(ctx, option: int, value: int):
+    ctx.check(ctx.lib.dock_set_option(ctx.h, int(option), int(value)), "dock_set_option")
+
+
+def get_option(ctx, option: int) -> int:
+    v = C.c_int()
+    ctx.check(ctx.lib.dock_get_option(ctx.h, int(option), C.byref(v)), "dock_get_option")
+    return v.value
 
 
 def dock_tune(ctx, grids, ligs, params: DockParams, what: int, cand, reps: int = 3) -> np.ndarray:

@@ -185,8 +185,11 @@ struct Task {
     unsigned long long seed;
 };
 
-template <int METHOD>
-__global__ void __launch_bounds__(128, 4)
+// MINB: blocks of 128 threads per SM the registers must leave room for (4:
+// <= 128 registers per thread, 3: <= 168, fewer spills); see
+// DOCK_OPT_BATCH_BLOCKS.
+template <int METHOD, int MINB>
+__global__ void __launch_bounds__(128, MINB)
 lga_persistent(const LigandDev *__restrict__ ligs, GridDev G, const Task *__restrict__ tasks, int n_tasks, int *next,
                BatchConst P, float *scratch, size_t floats_per_warp, int gmax, size_t smem_per_warp,
                float *best_geno, float *best_E32, unsigned long long *evals) {
@@ -279,7 +282,9 @@ extern "C" int dock_batch(dock_ctx *ctx, const dock_grids *grids, const dock_lig
         return set_err(ctx, DOCK_ERR_SIZE, "batch_warps: the block's shared memory does not fit");
     while (wpb > 1 && smem_per_warp * 4 * wpb > ctx->smem_optin) wpb >>= 1;
     const size_t smem = smem_per_warp * 4 * wpb;
-    auto kern = P.ls_method == 1 ? lga_persistent<1> : lga_persistent<0>;
+    const bool b3 = ctx->batch_min_blocks == 3;
+    auto kern = P.ls_method == 1 ? (b3 ? lga_persistent<1, 3> : lga_persistent<1, 4>)
+                                 : (b3 ? lga_persistent<0, 3> : lga_persistent<0, 4>);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e) return cuda_err(ctx, e, "dock_batch attributes");
@@ -387,7 +392,8 @@ __device__ __forceinline__ void warp_copy(T *dst, const volatile T *src, int lan
     for (int i = lane; i < (int)(sizeof(T) / 4); i += 32) d[i] = s[i];
 }
 
-__global__ void __launch_bounds__(128, 4)
+template <int MINB>
+__global__ void __launch_bounds__(128, MINB)
 lga_serve(const volatile ServeTask *tasks, const volatile ServeCtl *ctl, int capacity, ServeDev *q,
           float *scratch, size_t floats_per_warp, int pop_max, size_t smem_per_warp, float *best_geno,
           float *best_E32, double *best_E, unsigned long long *evals, volatile long long *done,
@@ -470,6 +476,9 @@ struct dock_server {
     cudaStream_t stream = nullptr;
     int capacity = 0, max_atoms = 0, pop_max = 0, warps = 0, wpb = 0, blocks = 0;
     size_t smem_per_warp = 0, smem = 0, floats_per_warp = 0;
+    void (*kernel)(const volatile ServeTask *, const volatile ServeCtl *, int, ServeDev *, float *, size_t, int,
+                   size_t, float *, float *, double *, unsigned long long *, volatile long long *,
+                   unsigned long long) = nullptr;  // lga_serve at the context's register cap
     ServeTask *tasks = nullptr;  // mapped host
     ServeCtl *ctl = nullptr;     // mapped host
     long long *done = nullptr;   // mapped host
@@ -510,9 +519,10 @@ int server_create(dock_ctx *ctx, int capacity, int max_atoms, int pop_max, dock_
     }
     S->smem = per_warp_bytes * S->wpb;
     cudaError_t e = cudaSuccess;
-    if (S->smem > 48 * 1024) e = cudaFuncSetAttribute(lga_serve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S->smem);
+    S->kernel = ctx->batch_min_blocks == 3 ? lga_serve<3> : lga_serve<4>;
+    if (S->smem > 48 * 1024) e = cudaFuncSetAttribute(S->kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S->smem);
     int per_sm = 0;
-    if (!e) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lga_serve, 32 * S->wpb, S->smem);
+    if (!e) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, S->kernel, 32 * S->wpb, S->smem);
     if (e || per_sm < 1) {
         delete S;
         return e ? cuda_err(ctx, e, "server_create occupancy") : set_err(ctx, DOCK_ERR_SIZE, "no occupancy");
@@ -560,7 +570,7 @@ static int server_kick(dock_server *S) {
     if (S->launched && cudaEventQuery(S->running) == cudaErrorNotReady) return DOCK_OK;
     cudaGetLastError();
     const unsigned long long max_idle = 1000000000ull;  // the kernel ends after a second without claims
-    lga_serve<<<S->blocks, 32 * S->wpb, S->smem, S->stream>>>(
+    S->kernel<<<S->blocks, 32 * S->wpb, S->smem, S->stream>>>(
         S->d_tasks, S->d_ctl, S->capacity, S->q, S->scratch, S->floats_per_warp, S->pop_max, S->smem_per_warp,
         S->best_geno, S->best_E32, S->best_E, S->evals, S->d_done, max_idle);
     ++S->ctx->launches;
@@ -675,9 +685,11 @@ int server_destroy(dock_server *S) {
 // Device time of dock_batch at warps-per-block `wpb` (autotuning): reps
 // calls after one untimed call, outputs into scratch.
 int tune_batch_launch(dock_ctx *ctx, const dock_grids *grids, const dock_ligand *const *ligs, int n_ligs,
-                      const dock_params &P0, int wpb, int reps, double *ms) {
+                      const dock_params &P0, int wpb, int min_blocks, int reps, double *ms) {
     dock_params P = P0;
-    P.batch_warps = wpb;
+    if (wpb) P.batch_warps = wpb;
+    const int keep = ctx->batch_min_blocks;
+    if (min_blocks) ctx->batch_min_blocks = min_blocks;
     const size_t rows = (size_t)n_ligs * P.nruns;
     const int gmax = 7 + DOCK_MAX_TORSIONS;
     cudaStream_t s = nullptr;
@@ -698,6 +710,7 @@ int tune_batch_launch(dock_ctx *ctx, const dock_grids *grids, const dock_ligand 
         if (!rc && e) rc = cuda_err(ctx, e, "dock_tune timing");
         if (!rc) *ms = t / reps;
     }
+    ctx->batch_min_blocks = keep;
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     dev_free(ctx, g, s);

@@ -264,9 +264,15 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
     float4 *PF = reinterpret_cast<float4 *>(ws + Y.pf);
     float *red = ws + Y.red;
     const int T = L.n_tors, N = L.n_atoms, NB = L.nb8;
-    // item i of a per-atom (or per-range) phase goes to warp i mod W, so the
-    // team's warps share the work evenly: first item of this thread
-    const int i0 = lane * W + tm.warp();
+    // the per-atom grid phase gives each warp a contiguous run of ceil(N/W)
+    // atoms (an even split whose lanes touch consecutive float4 in shared
+    // memory, free of bank conflicts): this thread's atoms are i0, i0 + 32, ...
+    // below i1
+    const int chunk = (N + W - 1) / W;
+    const int i0 = tm.warp() * chunk + lane, i1 = min(N, (tm.warp() + 1) * chunk);
+    // partial-force rows of the W > 1 groups: NB + 4 float4 apart, so the two
+    // rows a quarter-warp reads at once fall on different banks
+    const int PS = NB + 4;
 
     // Warp 0: rigid-body transform and the torsion tree, one level at a time
     // (M_child = M_parent o L_k; torsion k is lane k < 32).
@@ -326,12 +332,12 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
         if (W == 1)
             for (int k = r; k < NB; k += S) Fv[k] = make_float4(0.f, 0.f, 0.f, 0.f);
         else
-            for (int k = r; k < 4 * W * NB; k += S) PF[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int k = r; k < 4 * W * PS; k += S) PF[k] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     tm.sync();
 
     // Atom positions relative to t (padding atoms up to a multiple of 8 at 0).
-    for (int i = i0; i < NB; i += S) {
+    for (int i = r; i < NB; i += S) {
         float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
         if (i < N) {
             const float4 p = ldg(L.ref + i);
@@ -350,7 +356,7 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
     const float tx = geno[0], ty = geno[1], tz = geno[2];
     const float tux = (tx - G.ox) * G.inv_h, tuy = (ty - G.oy) * G.inv_h, tuz = (tz - G.oz) * G.inv_h;
     AtomCells A0;
-    if (i0 < N) {
+    if (i0 < i1) {
         const float4 xi = X[i0];
         atom_fetch(G, ldg(G.map_of_type + (ldg(L.meta + i0) & 255)), ldg(L.ref + i0).w, fmaf(xi.x, G.inv_h, tux),
                    fmaf(xi.y, G.inv_h, tuy), fmaf(xi.z, G.inv_h, tuz), A0);
@@ -365,7 +371,7 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
         const SchedDev &SD = L.sched[W == 1 ? 0 : W == 2 ? 1 : W == 4 ? 2 : 3];
         const int w = tm.warp(), q = 4 * w + (lane >> 3), sl = lane & 7, gb = lane & ~7;
         const int nxt = gb | ((sl + 1) & 7);
-        float4 *pq = W == 1 ? Fv : PF + q * NB;  // W = 1: the step's groups touch disjoint atoms
+        float4 *pq = W == 1 ? Fv : PF + q * PS;  // W = 1: the step's groups touch disjoint atoms
         const int s0 = SD.base[w], s1 = s0 + SD.steps[w];
         // one round: the pair (own atom, atom 8B + (sl + d) mod 8) with
         // coefficients c; the force owed to the B atom travels one lane on
@@ -423,7 +429,7 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
         }
     }
     if (W == 1 && GRAD) __syncwarp();  // pair forces in Fv before the grid part is added
-    for (int i = i0; i < N; i += S) {
+    for (int i = i0; i < i1; i += 32) {
         if (i != i0) {
             const float4 xi = X[i];
             atom_fetch(G, ldg(G.map_of_type + (ldg(L.meta + i) & 255)), ldg(L.ref + i).w, fmaf(xi.x, G.inv_h, tux),
@@ -457,12 +463,14 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
         constexpr int NG = 4 * W;
         const int kl = lanes_log2(N, S, NG), k = 1 << kl, sub = r & (k - 1);
         for (int b0 = 0; b0 < N; b0 += (S >> kl)) {
-            const int i = b0 + ((lane >> kl) * W + tm.warp());
+            // each warp takes a contiguous run of 32 >> kl atoms (consecutive
+            // float4 across its lanes: no bank conflicts)
+            const int i = b0 + tm.warp() * (32 >> kl) + (lane >> kl);
             const bool act = i < N;
             float fx = 0.f, fy = 0.f, fz = 0.f;
             if (act)
                 for (int g = sub; g < NG; g += k) {
-                    const float4 v = PF[g * NB + i];
+                    const float4 v = PF[g * PS + i];
                     fx += v.x; fy += v.y; fz += v.z;
                 }
             group_sum3(fx, fy, fz, kl);

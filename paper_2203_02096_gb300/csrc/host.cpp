@@ -180,6 +180,34 @@ int dock_destroy(dock_ctx *ctx) {
     return DOCK_OK;
 }
 
+int dock_set_option(dock_ctx *ctx, int option, int value) {
+    if (!ctx) return DOCK_ERR_INVALID;
+    if (option == DOCK_OPT_SCORE_BLOCKS) {
+        if (value != 1 && value != 6 && value != 8) return set_err(ctx, DOCK_ERR_INVALID, "score blocks must be 1, 6 or 8");
+        ctx->score_min_blocks = value;
+        return DOCK_OK;
+    }
+    if (option == DOCK_OPT_BATCH_BLOCKS) {
+        if (value != 3 && value != 4) return set_err(ctx, DOCK_ERR_INVALID, "batch blocks must be 3 or 4");
+        ctx->batch_min_blocks = value;
+        return DOCK_OK;
+    }
+    return set_err(ctx, DOCK_ERR_INVALID, "unknown option");
+}
+
+int dock_get_option(const dock_ctx *ctx, int option, int *value) {
+    if (!ctx || !value) return DOCK_ERR_INVALID;
+    if (option == DOCK_OPT_SCORE_BLOCKS) {
+        *value = ctx->score_min_blocks;
+        return DOCK_OK;
+    }
+    if (option == DOCK_OPT_BATCH_BLOCKS) {
+        *value = ctx->batch_min_blocks;
+        return DOCK_OK;
+    }
+    return DOCK_ERR_INVALID;
+}
+
 const char *dock_last_error(const dock_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
 int dock_set_timing(dock_ctx *ctx, int enable) {

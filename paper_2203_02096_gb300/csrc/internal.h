@@ -96,7 +96,7 @@ __host__ __device__ inline EvalLayout eval_layout(int n_atoms, int n_frag, int n
     w.x = o; o += 4 * nb8 * W;        // a copy per warp
     w.f = o; o += grad ? 4 * nb8 : 0;
     w.tq = o; o += grad ? 4 * n_atoms : 0;
-    w.pf = o; o += (grad && W > 1) ? 4 * 4 * W * nb8 : 0;  // W = 1 adds straight into f
+    w.pf = o; o += (grad && W > 1) ? 4 * 4 * W * (nb8 + 4) : 0;  // rows nb8 + 4 apart; W = 1 adds straight into f
     w.total = round4(o);
     return w;
 }
@@ -123,6 +123,8 @@ struct dock_ctx {
     int64_t launches = 0;
     int *d_flag = nullptr;  // device error word: 0 = fine
     long long *h_status = nullptr;  // pinned host words read back by the Solis-Wets docking loop
+    int score_min_blocks = 1;       // register cap of the batched scorers (DOCK_OPT_SCORE_BLOCKS)
+    int batch_min_blocks = 4;       // register cap of the persistent docking kernel (DOCK_OPT_BATCH_BLOCKS)
 };
 
 struct dock_grids {
@@ -151,7 +153,7 @@ int kernel_id(dock_ctx *ctx, const char *name);
 long long *host_status(dock_ctx *ctx);
 int check_sw(dock_ctx *ctx, const dock_params &p);  // ls_method and Solis-Wets constants
 int tune_batch_launch(dock_ctx *ctx, const dock_grids *grids, const dock_ligand *const *ligs, int n_ligs,
-                      const dock_params &P, int wpb, int reps, double *ms);  // 2 pinned words, allocated on first use; NULL on failure
+                      const dock_params &P, int wpb, int min_blocks, int reps, double *ms);  // 2 pinned words, allocated on first use; NULL on failure
 void timing_begin(dock_ctx *ctx, int kid, cudaStream_t s, TimedLaunch *tl);
 void timing_end(dock_ctx *ctx, cudaStream_t s, TimedLaunch *tl);
 int check_maps(dock_ctx *ctx, const dock_grids *g, const dock_ligand *l);

@@ -6,8 +6,11 @@ namespace {
 
 constexpr int kScoreWarps = 4;  // warps per block of the batched evaluators
 
-template <bool GRAD>
-__global__ void __launch_bounds__(kScoreWarps * 32)
+// MINB: blocks per SM the register allocation must leave room for (the
+// register cap: 65536 / (128 MINB) registers per thread; 1 = the compiler's
+// own choice); chosen per context, see dock_set_option.
+template <bool GRAD, int MINB>
+__global__ void __launch_bounds__(kScoreWarps * 32, MINB)
 score_kernel(LigandDev L, GridDev G, const float *__restrict__ geno, int B, float *__restrict__ E,
              float *__restrict__ grad, EvalLayout W) {
     extern __shared__ float4 smem4[];
@@ -138,8 +141,15 @@ cudaError_t launch_score(dock_ctx *ctx, const LigandDev &L, const GridDev &G, co
     const float *gp = geno;
     float *ep = E, *grp = grad;
     void *args[] = {&l, &gg, &gp, &B, &ep, &grp, &W};
-    if (g) return launch_warps(ctx, score_kernel<true>, B, wpb, smem, s, "score_grad", args);
-    return launch_warps(ctx, score_kernel<false>, B, wpb, smem, s, "score", args);
+    const int mb = ctx->score_min_blocks;
+    if (g) {
+        if (mb == 8) return launch_warps(ctx, score_kernel<true, 8>, B, wpb, smem, s, "score_grad", args);
+        if (mb == 6) return launch_warps(ctx, score_kernel<true, 6>, B, wpb, smem, s, "score_grad", args);
+        return launch_warps(ctx, score_kernel<true, 1>, B, wpb, smem, s, "score_grad", args);
+    }
+    if (mb == 8) return launch_warps(ctx, score_kernel<false, 8>, B, wpb, smem, s, "score", args);
+    if (mb == 6) return launch_warps(ctx, score_kernel<false, 6>, B, wpb, smem, s, "score", args);
+    return launch_warps(ctx, score_kernel<false, 1>, B, wpb, smem, s, "score", args);
 }
 
 cudaError_t launch_pose(dock_ctx *ctx, const LigandDev &L, const float *geno, int B, float *xyz, cudaStream_t s) {

@@ -56,7 +56,7 @@ ga_kernel(LigandDev L, GridDev G, GaConst C, uint32_t gen, const float *__restri
     const dev::Team<1> tm(lane);
     const int item = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (item >= C.nruns * C.pop) return;
-    const int r = item / C.pop, s = item % C.pop, Gn = 7 + C.nt, nblk = 4 + C.nt;
+    const int r = item / C.pop, s = item % C.pop, Gn = 7 + C.nt;
     const float *old = pop_old + (size_t)r * C.pop * Gn;
     const float *Eo = E_old + (size_t)r * C.pop;
     float *child = pop_new + (size_t)item * Gn;
@@ -756,6 +756,59 @@ int tune_ls_launch(dock_ctx *ctx, const dock_grids *grids, const dock_ligand *li
     return rc;
 }
 
+// Device time of score_grad_batch over an initial population of
+// params.pop_size * nruns genotypes at register cap `mb`.
+int tune_score_launch(dock_ctx *ctx, const dock_grids *grids, const dock_ligand *lig, const dock_params &P, int mb,
+                      int reps, double *ms) {
+    *ms = -1.0;
+    int rc = check_maps(ctx, grids, lig);
+    if (rc) return rc;
+    const LigandDev &L = lig->dev;
+    const int B = P.pop_size * P.nruns, Gn = L.n_genes;
+    if (B < 1) return set_err(ctx, DOCK_ERR_INVALID, "dock_tune: empty batch");
+    cudaStream_t s = nullptr;
+    float *x = (float *)dev_alloc(ctx, (size_t)B * Gn * 4, s);
+    float *E = (float *)dev_alloc(ctx, (size_t)B * 4, s);
+    float *g = (float *)dev_alloc(ctx, (size_t)B * Gn * 4, s);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    const int keep = ctx->score_min_blocks;
+    cudaError_t e = cudaSuccess;
+    if (!x || !E || !g) {
+        rc = set_err(ctx, DOCK_ERR_OOM, "dock_tune: allocation failed");
+    } else {
+        dock_params Q = P;
+        Q.pop_size = B;
+        GaConst C = ga_const(Q, L.n_tors, 1, 0x7475u);
+        LigandDev l{};
+        l.n_tors = L.n_tors;
+        GridDev gd = grids->dev;
+        EvalLayout w = eval_layout(1, 1, 8, false, 1);
+        float *no_e = nullptr;
+        unsigned long long *no_ev = nullptr;
+        void *a[] = {&l, &gd, &C, &x, &no_e, &no_ev, &w};
+        e = launch_items(ctx, init_kernel<false>, B, 4, (size_t)w.total * 16, s, "tune_init", a);
+        ctx->score_min_blocks = mb;
+        if (!e) e = launch_score(ctx, L, grids->dev, x, B, E, g, s);
+        if (!e) e = cudaEventCreate(&e0);
+        if (!e) e = cudaEventCreate(&e1);
+        if (!e) e = cudaEventRecord(e0, s);
+        for (int r = 0; r < reps && !e; ++r) e = launch_score(ctx, L, grids->dev, x, B, E, g, s);
+        if (!e) e = cudaEventRecord(e1, s);
+        if (!e) e = cudaEventSynchronize(e1);
+        float t = 0.f;
+        if (!e) e = cudaEventElapsedTime(&t, e0, e1);
+        ctx->score_min_blocks = keep;
+        if (e) rc = cuda_err(ctx, e, "dock_tune score");
+        else *ms = (double)t / reps;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    dev_free(ctx, x, s);
+    dev_free(ctx, E, s);
+    dev_free(ctx, g, s);
+    return rc;
+}
+
 extern "C" int dock_tune(dock_ctx *ctx, const dock_grids *grids, const dock_ligand *const *ligs, int n_ligs,
                          const dock_params *params, int what, const int *cand, int n_cand, int reps, double *ms) {
     if (!ctx) return DOCK_ERR_INVALID;
@@ -776,11 +829,22 @@ extern "C" int dock_tune(dock_ctx *ctx, const dock_grids *grids, const dock_liga
         } else if (what == DOCK_TUNE_BATCH_WARPS) {
             if (c != 1 && c != 2 && c != 4) return set_err(ctx, DOCK_ERR_INVALID, "dock_tune: warps must be 1, 2 or 4");
             ms[i] = -1.0;
-            rc = tune_batch_launch(ctx, grids, ligs, n_ligs, P, c, reps, &ms[i]);
+            rc = tune_batch_launch(ctx, grids, ligs, n_ligs, P, c, 0, reps, &ms[i]);
             if (rc == DOCK_ERR_SIZE) {  // this width does not fit: reported as -1
                 ms[i] = -1.0;
                 rc = DOCK_OK;
             }
+        } else if (what == DOCK_TUNE_BATCH_BLOCKS) {
+            if (c != 3 && c != 4) return set_err(ctx, DOCK_ERR_INVALID, "dock_tune: batch blocks must be 3 or 4");
+            ms[i] = -1.0;
+            rc = tune_batch_launch(ctx, grids, ligs, n_ligs, P, 0, c, reps, &ms[i]);
+            if (rc == DOCK_ERR_SIZE) {
+                ms[i] = -1.0;
+                rc = DOCK_OK;
+            }
+        } else if (what == DOCK_TUNE_SCORE_BLOCKS) {
+            if (c != 1 && c != 6 && c != 8) return set_err(ctx, DOCK_ERR_INVALID, "dock_tune: blocks must be 1, 6 or 8");
+            rc = tune_score_launch(ctx, grids, ligs[0], P, c, reps, &ms[i]);
         } else {
             return set_err(ctx, DOCK_ERR_INVALID, "dock_tune: unknown kernel family");
         }

@@ -59,3 +59,43 @@ def test_tune_rejects_bad_requests(gpu, drug_system):
         capi.dock_tune(gpu, G, [L], P, capi.TUNE_LS_THREADS, [48])
     with pytest.raises(capi.DockError):
         capi.dock_batch(gpu, G, [L], capi.default_params(nruns=2, batch_warps=3))
+
+
+def test_score_register_caps_do_not_change_results(gpu, drug_system, tmp_path):
+    """score_grad_batch at every register cap gives the same bits; the tuner
+    times them and sets its choice on the context."""
+    L = capi.ligand_from(gpu, synth.make_ligand(64, 16, seed=0))
+    G = capi.grids_from_maps(gpu, drug_system["maps"], drug_system["box"])
+    x = torch.from_numpy(synth.make_genotypes(4099, L.n_torsions, drug_system["box"], seed=2)).cuda()
+    res = []
+    for b in (1, 6, 8):
+        capi.set_option(gpu, capi.OPT_SCORE_BLOCKS, b)
+        assert capi.get_option(gpu, capi.OPT_SCORE_BLOCKS) == b
+        res.append(capi.score_grad_batch(gpu, G, L, x))
+    capi.set_option(gpu, capi.OPT_SCORE_BLOCKS, 1)
+    for E, g in res[1:]:
+        assert torch.equal(E, res[0][0]) and torch.equal(g, res[0][1])
+    t = autotune.Tuner(gpu, path=str(tmp_path / "tune.json"))
+    b = t.score_blocks(G, L, batch=8192)
+    assert b in autotune.SCORE_BLOCK_CANDIDATES and capi.get_option(gpu, capi.OPT_SCORE_BLOCKS) == b
+    capi.set_option(gpu, capi.OPT_SCORE_BLOCKS, 1)
+    with pytest.raises(capi.DockError):
+        capi.set_option(gpu, capi.OPT_SCORE_BLOCKS, 3)
+
+
+def test_batch_register_caps_do_not_change_results(gpu, drug_system):
+    rng = np.random.default_rng(4)
+    ligs = [synth.make_ligand(int(rng.integers(10, 109)), int(rng.integers(0, 33)), seed=700 + k) for k in range(6)]
+    L = [capi.ligand_from(gpu, l) for l in ligs]
+    G = capi.grids_from_maps(gpu, drug_system["maps"], drug_system["box"])
+    P = capi.default_params(pop_size=30, nruns=2, max_evals=1500, ls_iters=10)
+    outs = []
+    for b in (4, 3):
+        capi.set_option(gpu, capi.OPT_BATCH_BLOCKS, b)
+        outs.append(capi.dock_batch(gpu, G, L, P, np.arange(6, dtype=np.uint64)))
+    capi.set_option(gpu, capi.OPT_BATCH_BLOCKS, 4)
+    torch.cuda.synchronize()
+    for k in ("best_geno", "best_E", "evals"):
+        assert torch.equal(outs[0][k], outs[1][k]), k
+    ms = capi.dock_tune(gpu, G, L, P, capi.TUNE_BATCH_BLOCKS, [4, 3], 1)
+    assert np.all(ms > 0)
