@@ -128,19 +128,46 @@ __device__ __forceinline__ float trilinear(const Cell8 &v, const CellPos &c, flo
     return fmaf(c.fz, y1 - y0, y0);
 }
 
-// An atom's grid reads, issued before they are needed.
+// An atom's grid cells and where it sits in them.
 struct AtomCells {
     CellPos c;
     Cell8 t, e, d;
     float q;
 };
 
-__device__ __forceinline__ void atom_fetch(const GridDev &G, int map_t, float q, float ux, float uy, float uz,
-                                           AtomCells &A) {
+
+// Asynchronous staging of an atom's three map cells (type, electrostatic,
+// desolvation; two float4 each) into shared memory with cp.async: 16-byte
+// global->shared copies that use no registers, so every atom's L2 reads are
+// in flight while the pair rounds run.  The copying thread waits for its own
+// copies (cp.async.wait_all) before it reads them back.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+__device__ __forceinline__ void atom_stage(const GridDev &G, int map_t, float ux, float uy, float uz, float4 *dst) {
+    CellPos c;
+    locate(G, ux, uy, uz, c);
+    const float4 *b = G.cells + 2 * ((size_t)c.cell * G.M);
+    cp_async16(dst + 0, b + 2 * map_t);
+    cp_async16(dst + 1, b + 2 * map_t + 1);
+    cp_async16(dst + 2, b + 2 * G.emap);
+    cp_async16(dst + 3, b + 2 * G.emap + 1);
+    cp_async16(dst + 4, b + 2 * G.dmap);
+    cp_async16(dst + 5, b + 2 * G.dmap + 1);
+}
+
+// The staged cells of an atom back as AtomCells (its cell position located
+// again from the same coordinates).
+__device__ __forceinline__ void atom_unstage(const GridDev &G, float q, float ux, float uy, float uz,
+                                             const float4 *src, AtomCells &A) {
     locate(G, ux, uy, uz, A.c);
-    A.t = load_cell(G, A.c.cell, map_t);
-    A.e = load_cell(G, A.c.cell, G.emap);
-    A.d = load_cell(G, A.c.cell, G.dmap);
+    A.t = Cell8{src[0], src[1]};
+    A.e = Cell8{src[2], src[3]};
+    A.d = Cell8{src[4], src[5]};
     A.q = q;
 }
 
@@ -351,16 +378,18 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
     }
     tm.sync();
 
-    // Particle-grid reads of the thread's first atom go out first; the pair
-    // rounds run while they are in flight.
+    // Particle-grid reads of the thread's atoms go out first, staged into
+    // shared memory asynchronously; the pair rounds run while they are in
+    // flight.
     const float tx = geno[0], ty = geno[1], tz = geno[2];
     const float tux = (tx - G.ox) * G.inv_h, tuy = (ty - G.oy) * G.inv_h, tuz = (tz - G.oz) * G.inv_h;
-    AtomCells A0;
-    if (i0 < i1) {
-        const float4 xi = X[i0];
-        atom_fetch(G, ldg(G.map_of_type + (ldg(L.meta + i0) & 255)), ldg(L.ref + i0).w, fmaf(xi.x, G.inv_h, tux),
-                   fmaf(xi.y, G.inv_h, tuy), fmaf(xi.z, G.inv_h, tuz), A0);
+    float4 *Cst = reinterpret_cast<float4 *>(ws + Y.cst);
+    for (int i = i0; i < i1; i += 32) {
+        const float4 xi = X[i];
+        atom_stage(G, ldg(G.map_of_type + (ldg(L.meta + i) & 255)), fmaf(xi.x, G.inv_h, tux),
+                   fmaf(xi.y, G.inv_h, tuy), fmaf(xi.z, G.inv_h, tuz), Cst + 6 * i);
     }
+    cp_async_commit();
 
     // Intramolecular pairs, systolic: in a step, lane l of group q holds its
     // own atom of block A and, passed one lane along per round, the force
@@ -429,12 +458,12 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
         }
     }
     if (W == 1 && GRAD) __syncwarp();  // pair forces in Fv before the grid part is added
+    cp_async_wait_all();
     for (int i = i0; i < i1; i += 32) {
-        if (i != i0) {
-            const float4 xi = X[i];
-            atom_fetch(G, ldg(G.map_of_type + (ldg(L.meta + i) & 255)), ldg(L.ref + i).w, fmaf(xi.x, G.inv_h, tux),
-                       fmaf(xi.y, G.inv_h, tuy), fmaf(xi.z, G.inv_h, tuz), A0);
-        }
+        const float4 xi = X[i];
+        AtomCells A0;
+        atom_unstage(G, ldg(L.ref + i).w, fmaf(xi.x, G.inv_h, tux), fmaf(xi.y, G.inv_h, tuy),
+                     fmaf(xi.z, G.inv_h, tuz), Cst + 6 * i, A0);
         float3 g;
         e += atom_grid_energy<GRAD>(G, A0, g);
         if (GRAD) {

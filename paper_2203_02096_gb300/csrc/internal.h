@@ -79,7 +79,7 @@ struct GridDev {
 // Shared-memory scratch of one evaluating team, offsets in floats (each a
 // multiple of 4 so float4 views are aligned).
 struct EvalLayout {
-    int geno, grad, red, M, fs, x, f, tq, pf, total;
+    int geno, grad, red, M, fs, x, f, tq, pf, cst, total;
 };
 
 __host__ __device__ inline int round4(int v) { return (v + 3) & ~3; }
@@ -97,6 +97,7 @@ __host__ __device__ inline EvalLayout eval_layout(int n_atoms, int n_frag, int n
     w.f = o; o += grad ? 4 * nb8 : 0;
     w.tq = o; o += grad ? 4 * n_atoms : 0;
     w.pf = o; o += (grad && W > 1) ? 4 * 4 * W * (nb8 + 4) : 0;  // rows nb8 + 4 apart; W = 1 adds straight into f
+    w.cst = o; o += 24 * nb8;  // staged map cells: 6 float4 per atom
     w.total = round4(o);
     return w;
 }
