@@ -283,6 +283,10 @@ def run(args):
     ls_avg_s = ls_ms / max(ls_n, 1) / 1e3
     achieved = f_eval * evals_per_ls_launch / ls_avg_s / 1e12
     peak = peak_fp32_tflops()
+    # measured device rates (microbenchmarks, untimed): context for the roofline
+    measured = {"ffma_tflops": capi.microbench(ctx, capi.PEAK_FFMA),
+                "ex2_gops": capi.microbench(ctx, capi.PEAK_EX2),
+                "l2_read_gbs": capi.microbench(ctx, capi.PEAK_L2_READ)}
 
     # ---- end to end through the public API with host buffers
     e2e_steps = max(1, min(args.steps, 3))
@@ -330,7 +334,11 @@ def run(args):
                          "flops_per_eval": f_eval, "evals_per_launch": evals_per_ls_launch,
                          "launch_ms": ls_avg_s * 1e3, "launches": ls_n,
                          "l2_bytes_per_eval": grid_bytes_per_eval(w.ligand.n_atoms),
-                         "l2_achieved_gbs": grid_bytes_per_eval(w.ligand.n_atoms) * evals_per_ls_launch / ls_avg_s / 1e9},
+                         "l2_achieved_gbs": grid_bytes_per_eval(w.ligand.n_atoms) * evals_per_ls_launch / ls_avg_s / 1e9,
+                         "measured_rates": measured,
+                         "frac_of_measured_ffma": achieved / measured["ffma_tflops"],
+                         "l2_frac_of_measured": grid_bytes_per_eval(w.ligand.n_atoms) * evals_per_ls_launch / ls_avg_s
+                         / 1e9 / measured["l2_read_gbs"]},
             "kernel_share": {"dock_ls": ls_ms / sum(step_ms), "dock_ga": ga_ms / sum(step_ms)},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": int(launches),
@@ -388,10 +396,14 @@ def score_grad_throughput(ctx, G, box, dev, reps: int = 5):
     L.free()
     capi.set_option(ctx, capi.OPT_SCORE_BLOCKS, 1)
     achieved = f * 65536 / t / 1e12
+    ffma, l2 = capi.microbench(ctx, capi.PEAK_FFMA), capi.microbench(ctx, capi.PEAK_L2_READ)
     return {"workload": "65536 genotypes, 64 atoms / 16 torsions, 64^3 x 9 maps", "evals_per_s": 65536 / t,
             "launch_ms": t * 1e3, "flops_per_eval": f, "achieved_tflops": achieved,
             "frac_fp32_peak": achieved / peak_fp32_tflops(),
             "l2_achieved_gbs": grid_bytes_per_eval(lig.n_atoms) * 65536 / t / 1e9,
+            "frac_of_measured_ffma": achieved / ffma, "measured_ffma_tflops": ffma,
+            "l2_frac_of_measured": grid_bytes_per_eval(lig.n_atoms) * 65536 / t / 1e9 / l2,
+            "measured_l2_read_gbs": l2,
             "autotuned_score_blocks": blocks, "score_blocks_ms": tuner.curve("|score|")}
 
 
@@ -611,17 +623,21 @@ def pair_list(lig):
 # digest of the kernel sources and input generator it was taken on: the figure
 # is reported only while they are unchanged.
 LS_TRAFFIC_BYTES = 55.40e6
-LS_TRAFFIC_SOURCES = "0688e9b9e45368d5"
+LS_TRAFFIC_SOURCES = "e24790f07865aabc"
+
+
+# the files that define the local-search kernel and the ligand it runs on
+LS_SOURCES = ("csrc/eval.cuh", "csrc/ga.cuh", "csrc/search.cu", "csrc/internal.h", "csrc/forcefield.h",
+              "csrc/host.cpp", "synth.py")
 
 
 def sources_digest() -> str:
-    import glob
     import hashlib
     pkg = os.path.join(ROOT, "paper_2203_02096_gb300")
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(pkg, "csrc", "*"))) + [os.path.join(pkg, "synth.py")]:
-        h.update(os.path.basename(f).encode())
-        with open(f, "rb") as fh:
+    for rel in LS_SOURCES:
+        h.update(os.path.basename(rel).encode())
+        with open(os.path.join(pkg, rel), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 

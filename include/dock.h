@@ -259,6 +259,19 @@ int dock_tune(dock_ctx *ctx, const dock_grids *grids, const dock_ligand *const *
 int dock_set_option(dock_ctx *ctx, int option, int value);
 int dock_get_option(const dock_ctx *ctx, int option, int *value);
 
+/* ---- device rates for the rooflines (no paper counterpart) ----
+ * dock_microbench measures one rate of this device with a microbenchmark
+ * kernel (best of three timed launches after a warm-up launch):
+ *   DOCK_PEAK_FFMA: FP32 fused multiply-add throughput, TFLOP/s (2 FLOP each);
+ *   DOCK_PEAK_EX2: special-function ex2.approx throughput, Gop/s;
+ *   DOCK_PEAK_L2_READ: L2->SM load bandwidth over a 48 MB L2-resident
+ *     buffer read with ld.global.cg, GB/s.
+ * *value receives the rate.  Errors: unknown `what`, allocation failure. */
+#define DOCK_PEAK_FFMA 1
+#define DOCK_PEAK_EX2 2
+#define DOCK_PEAK_L2_READ 3
+int dock_microbench(dock_ctx *ctx, int what, double *value);
+
 /* ---- serving: continuous batching of docking requests ----
  * A server keeps a persistent docking kernel fed from a queue: each request
  * (one ligand, its grids, params and seed) becomes nruns tasks; warps of the

@@ -15,7 +15,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "libdock.so")
 BUILD = os.path.join(PKG, "_build")
-SOURCES = ["host.cpp", "score.cu", "search.cu", "grids.cu", "batch.cu"]
+SOURCES = ["host.cpp", "score.cu", "search.cu", "grids.cu", "batch.cu", "peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

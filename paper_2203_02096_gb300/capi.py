@@ -81,6 +81,7 @@ SIGNATURES = {
     "dock_philox": (_i, [_vp, _vp, _i, _u32, _u32, _vp, _vp]),
     "dock_tune": (_i, [_vp, _vp, _vp, _i, _P(DockParams), _i, _vp, _i, _i, _vp]),
     "dock_set_option": (_i, [_vp, _i, _i]),
+    "dock_microbench": (_i, [_vp, _i, _P(_d)]),
     "dock_get_option": (_i, [_vp, _i, _P(_i)]),
     "dock_solis_wets": (_i, [_vp, _vp, _vp, _vp, _vp, _i, _P(DockParams), _u64, _u32, _u32, _vp, _vp, _vp, _vp]),
     "dock_set_timing": (_i, [_vp, _i]),
@@ -470,6 +471,16 @@ TUNE_SCORE_BLOCKS = 3
 TUNE_BATCH_BLOCKS = 4
 OPT_SCORE_BLOCKS = 1
 OPT_BATCH_BLOCKS = 2
+
+
+PEAK_FFMA, PEAK_EX2, PEAK_L2_READ = 1, 2, 3
+
+
+def microbench(ctx, what: int) -> float:
+    """A measured device rate: TFLOP/s (FFMA), Gop/s (ex2) or GB/s (L2 read)."""
+    v = C.c_double()
+    ctx.check(ctx.lib.dock_microbench(ctx.h, int(what), C.byref(v)), "dock_microbench")
+    return v.value
 
 
 def set_option(ctx, option: int, value: int):

@@ -99,3 +99,14 @@ def test_batch_register_caps_do_not_change_results(gpu, drug_system):
         assert torch.equal(outs[0][k], outs[1][k]), k
     ms = capi.dock_tune(gpu, G, L, P, capi.TUNE_BATCH_BLOCKS, [4, 3], 1)
     assert np.all(ms > 0)
+
+
+def test_microbenchmarks_report_plausible_rates(gpu):
+    """The roofline denominators measured on the device: FP32 FMA within
+    (10, 120) TFLOP/s, ex2 within (100, 20000) Gop/s, L2 reads within
+    (500, 50000) GB/s -- wide bands around GB300's unit counts."""
+    assert 10 < capi.microbench(gpu, capi.PEAK_FFMA) < 120
+    assert 100 < capi.microbench(gpu, capi.PEAK_EX2) < 20000
+    assert 500 < capi.microbench(gpu, capi.PEAK_L2_READ) < 50000
+    with pytest.raises(capi.DockError):
+        capi.microbench(gpu, 99)
