@@ -301,8 +301,12 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
     // rows a quarter-warp reads at once fall on different banks
     const int PS = NB + 4;
 
-    // Warp 0: rigid-body transform and the torsion tree, one level at a time
-    // (M_child = M_parent o L_k; torsion k is lane k < 32).
+    // Warp 0: rigid-body transform and the torsion tree.  Torsion k is lane
+    // k < 32; its fragment's full transform M_{k+1} = M_0 o L_a o ... o L_k
+    // is built by pointer jumping over the tree: each round composes a
+    // lane's partial product with its current ancestor's and jumps to that
+    // ancestor's ancestor, so depth d takes ceil(log2 d) + 1 rounds of
+    // shuffles instead of d rounds through shared memory.
     if (tm.warp() == 0) {
         __syncwarp();
         float qw = geno[3], qx = geno[4], qy = geno[5], qz = geno[6];
@@ -313,13 +317,17 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
         } else {
             qw = 1.f; qx = qy = qz = 0.f;
         }
+        // M_0: the rotation of the normalised quaternion (no translation)
+        const float q00 = 1.f - 2.f * (qy * qy + qz * qz), q01 = 2.f * (qx * qy - qw * qz), q02 = 2.f * (qx * qz + qw * qy);
+        const float q10 = 2.f * (qx * qy + qw * qz), q11 = 1.f - 2.f * (qx * qx + qz * qz), q12 = 2.f * (qy * qz - qw * qx);
+        const float q20 = 2.f * (qx * qz - qw * qy), q21 = 2.f * (qy * qz + qw * qx), q22 = 1.f - 2.f * (qx * qx + qy * qy);
         if (lane == 0) {
-            M[0] = make_float4(1.f - 2.f * (qy * qy + qz * qz), 2.f * (qx * qy - qw * qz), 2.f * (qx * qz + qw * qy), 0.f);
-            M[1] = make_float4(2.f * (qx * qy + qw * qz), 1.f - 2.f * (qx * qx + qz * qz), 2.f * (qy * qz - qw * qx), 0.f);
-            M[2] = make_float4(2.f * (qx * qz - qw * qy), 2.f * (qy * qz + qw * qx), 1.f - 2.f * (qx * qx + qy * qy), 0.f);
+            M[0] = make_float4(q00, q01, q02, 0.f);
+            M[1] = make_float4(q10, q11, q12, 0.f);
+            M[2] = make_float4(q20, q21, q22, 0.f);
         }
         float r00 = 0, r01 = 0, r02 = 0, r10 = 0, r11 = 0, r12 = 0, r20 = 0, r21 = 0, r22 = 0, t0 = 0, t1 = 0, t2 = 0;
-        int depth = 0, parent = 0;
+        int up = 0;         // fragment the lane's partial product reaches up to (0: the root, done)
         if (lane < T) {
             // reduce to [-pi, pi] (one multiple of 2 pi), then the fast intrinsic
             float tau = geno[ldg(L.tors_gene + lane)];
@@ -334,22 +342,43 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
             t0 = b.x - (r00 * b.x + r01 * b.y + r02 * b.z);
             t1 = b.y - (r10 * b.x + r11 * b.y + r12 * b.z);
             t2 = b.z - (r20 * b.x + r21 * b.y + r22 * b.z);
-            const int4 fr = ldg(L.frag + lane + 1);
-            parent = fr.z;
-            depth = fr.w;
+            up = ldg(L.frag + lane + 1).z;
         }
-        for (int d = 1; d <= L.max_depth; ++d) {
-            __syncwarp();
-            if (lane < T && depth == d) {
-                const float4 p0 = M[3 * parent], p1 = M[3 * parent + 1], p2 = M[3 * parent + 2];
-                float4 *o = M + 3 * (lane + 1);
-                o[0] = make_float4(p0.x * r00 + p0.y * r10 + p0.z * r20, p0.x * r01 + p0.y * r11 + p0.z * r21,
-                                   p0.x * r02 + p0.y * r12 + p0.z * r22, p0.x * t0 + p0.y * t1 + p0.z * t2 + p0.w);
-                o[1] = make_float4(p1.x * r00 + p1.y * r10 + p1.z * r20, p1.x * r01 + p1.y * r11 + p1.z * r21,
-                                   p1.x * r02 + p1.y * r12 + p1.z * r22, p1.x * t0 + p1.y * t1 + p1.z * t2 + p1.w);
-                o[2] = make_float4(p2.x * r00 + p2.y * r10 + p2.z * r20, p2.x * r01 + p2.y * r11 + p2.z * r21,
-                                   p2.x * r02 + p2.y * r12 + p2.z * r22, p2.x * t0 + p2.y * t1 + p2.z * t2 + p2.w);
+        // (A o B): rotation R_A R_B, translation R_A t_B + t_A; A = (a.., ta..)
+        auto compose = [&](float a00, float a01, float a02, float a10, float a11, float a12, float a20, float a21,
+                           float a22, float ta0, float ta1, float ta2) {
+            const float n00 = a00 * r00 + a01 * r10 + a02 * r20, n01 = a00 * r01 + a01 * r11 + a02 * r21;
+            const float n02 = a00 * r02 + a01 * r12 + a02 * r22;
+            const float n10 = a10 * r00 + a11 * r10 + a12 * r20, n11 = a10 * r01 + a11 * r11 + a12 * r21;
+            const float n12 = a10 * r02 + a11 * r12 + a12 * r22;
+            const float n20 = a20 * r00 + a21 * r10 + a22 * r20, n21 = a20 * r01 + a21 * r11 + a22 * r21;
+            const float n22 = a20 * r02 + a21 * r12 + a22 * r22;
+            const float m0 = a00 * t0 + a01 * t1 + a02 * t2 + ta0, m1 = a10 * t0 + a11 * t1 + a12 * t2 + ta1;
+            const float m2 = a20 * t0 + a21 * t1 + a22 * t2 + ta2;
+            r00 = n00; r01 = n01; r02 = n02; r10 = n10; r11 = n11; r12 = n12; r20 = n20; r21 = n21; r22 = n22;
+            t0 = m0; t1 = m1; t2 = m2;
+        };
+        if (lane < T && up == 0) compose(q00, q01, q02, q10, q11, q12, q20, q21, q22, 0.f, 0.f, 0.f);
+        // at most 6 rounds: depth <= 32 = 2^5
+        for (int jump = 0; jump < 6 && __any_sync(0xffffffffu, lane < T && up != 0); ++jump) {
+            const int src = up > 0 ? up - 1 : lane;  // lane holding fragment `up`
+            const float a00 = __shfl_sync(0xffffffffu, r00, src), a01 = __shfl_sync(0xffffffffu, r01, src);
+            const float a02 = __shfl_sync(0xffffffffu, r02, src), a10 = __shfl_sync(0xffffffffu, r10, src);
+            const float a11 = __shfl_sync(0xffffffffu, r11, src), a12 = __shfl_sync(0xffffffffu, r12, src);
+            const float a20 = __shfl_sync(0xffffffffu, r20, src), a21 = __shfl_sync(0xffffffffu, r21, src);
+            const float a22 = __shfl_sync(0xffffffffu, r22, src), b0 = __shfl_sync(0xffffffffu, t0, src);
+            const float b1 = __shfl_sync(0xffffffffu, t1, src), b2 = __shfl_sync(0xffffffffu, t2, src);
+            const int up2 = __shfl_sync(0xffffffffu, up, src);
+            if (lane < T && up != 0) {
+                compose(a00, a01, a02, a10, a11, a12, a20, a21, a22, b0, b1, b2);
+                up = up2;
             }
+        }
+        if (lane < T) {
+            float4 *o = M + 3 * (lane + 1);
+            o[0] = make_float4(r00, r01, r02, t0);
+            o[1] = make_float4(r10, r11, r12, t1);
+            o[2] = make_float4(r20, r21, r22, t2);
         }
     }
     // Force accumulators start at zero: W = 1 adds pair forces straight into
@@ -479,9 +508,9 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
     if (!GRAD) return team_sum(tm, e, red);
     tm.sync();
 
-    // Per-atom force = grid part + the 4W group partials (2^kl lanes per atom,
-    // partials in group order, butterfly); torque (x_i - t) x f_i.  W = 1:
-    // the forces are complete already.
+    // Per-atom force = grid part + the partial rows of the groups that
+    // touched the atom's block; torque (x_i - t) x f_i.  W = 1: the forces
+    // are complete already.
     float4 *Tq = reinterpret_cast<float4 *>(ws + Y.tq);
     if (W == 1) {
         for (int i = r; i < N; i += S) {
@@ -489,26 +518,21 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
             Tq[i] = make_float4(xi.y * f.z - xi.z * f.y, xi.z * f.x - xi.x * f.z, xi.x * f.y - xi.y * f.x, 0.f);
         }
     } else {
-        constexpr int NG = 4 * W;
-        const int kl = lanes_log2(N, S, NG), k = 1 << kl, sub = r & (k - 1);
-        for (int b0 = 0; b0 < N; b0 += (S >> kl)) {
-            // each warp takes a contiguous run of 32 >> kl atoms (consecutive
-            // float4 across its lanes: no bank conflicts)
-            const int i = b0 + tm.warp() * (32 >> kl) + (lane >> kl);
-            const bool act = i < N;
-            float fx = 0.f, fy = 0.f, fz = 0.f;
-            if (act)
-                for (int g = sub; g < NG; g += k) {
-                    const float4 v = PF[g * PS + i];
-                    fx += v.x; fy += v.y; fz += v.z;
-                }
-            group_sum3(fx, fy, fz, kl);
-            if (act && sub == 0) {
-                const float4 g = Fv[i], xi = X[i];
-                fx += g.x; fy += g.y; fz += g.z;
-                Fv[i] = make_float4(fx, fy, fz, 0.f);
-                Tq[i] = make_float4(xi.y * fz - xi.z * fy, xi.z * fx - xi.x * fz, xi.x * fy - xi.y * fx, 0.f);
+        // atom i sums the partial rows of the groups whose steps touched its
+        // block (ascending group order), then adds its grid force
+        const uint32_t *gmask = L.sched[W == 2 ? 1 : W == 4 ? 2 : 3].gmask;
+        for (int i = r; i < N; i += S) {
+            uint32_t m = ldg(gmask + (i >> 3));
+            const float4 gr = Fv[i], xi = X[i];
+            float fx = gr.x, fy = gr.y, fz = gr.z;
+            while (m) {
+                const int g = __ffs(m) - 1;
+                m &= m - 1;
+                const float4 v = PF[g * PS + i];
+                fx += v.x; fy += v.y; fz += v.z;
             }
+            Fv[i] = make_float4(fx, fy, fz, 0.f);
+            Tq[i] = make_float4(xi.y * fz - xi.z * fy, xi.z * fx - xi.x * fz, xi.x * fy - xi.y * fx, 0.f);
         }
     }
     tm.sync();

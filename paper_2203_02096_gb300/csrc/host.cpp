@@ -430,6 +430,7 @@ struct Blob {
 struct SchedHost {
     std::vector<uint32_t> ctrl;
     std::vector<float4> rec;
+    std::vector<uint32_t> gmask;  // per block: bit q set when group q's partial row holds forces of its atoms
     int base[8] = {0}, steps[8] = {0};
     double listed = 0;  // pair slots weighted by how often a step meets them; must equal the pair count
 };
@@ -515,6 +516,7 @@ SchedHost build_sched(int n, int W, const std::vector<int> &pidx, const std::vec
         off += R;
     }
     const size_t ns = (size_t)std::max(off, 1);
+    S.gmask.assign((size_t)std::max(nb, 1), 0u);
     S.ctrl.assign(ns * 4, 0u);
     S.rec.assign(ns * 256, make_float4(0.f, 0.f, 0.f, 0.f));
     for (int w = 0; w < W; ++w)
@@ -529,6 +531,8 @@ SchedHost build_sched(int n, int W, const std::vector<int> &pidx, const std::vec
                 }
                 const int A = bps[bi].first, B = bps[bi].second;
                 const bool diag = A == B;
+                S.gmask[A] |= 1u << (4 * w + q);
+                S.gmask[B] |= 1u << (4 * w + q);
                 S.ctrl[4 * (size_t)st + q] = (uint32_t)A | ((uint32_t)B << 5) | SCH_VALID | (hs ? SCH_HALF : 0u);
                 for (int d = hs ? 1 : 0; d < (hs ? 5 : 8); ++d)
                     for (int sl = 0; sl < 8; ++sl) {
@@ -774,10 +778,11 @@ extern "C" int load_ligand(dock_ctx *ctx, int n, const double *xyz, const int *t
     const size_t o_r64 = B.add(ref64.data(), 3 * n * sizeof(double));
     const size_t o_pc64 = B.add(pc64.data(), pc64.size() * sizeof(double));
     const size_t o_q64 = B.add(q64.data(), n * sizeof(double));
-    size_t o_sc[4], o_sr[4];
+    size_t o_sc[4], o_sr[4], o_sm[4];
     for (int k = 0; k < 4; ++k) {
         o_sc[k] = B.add(sched[k].ctrl.data(), sched[k].ctrl.size() * sizeof(uint32_t));
         o_sr[k] = B.add(sched[k].rec.data(), sched[k].rec.size() * sizeof(float4));
+        o_sm[k] = B.add(sched[k].gmask.data(), sched[k].gmask.size() * sizeof(uint32_t));
     }
 
     dock_ligand *L = new dock_ligand();
@@ -823,6 +828,7 @@ extern "C" int load_ligand(dock_ctx *ctx, int n, const double *xyz, const int *t
     for (int k = 0; k < 4; ++k) {
         d.sched[k].ctrl = (const uint32_t *)(base + o_sc[k]);
         d.sched[k].rec = (const float4 *)(base + o_sr[k]);
+        d.sched[k].gmask = (const uint32_t *)(base + o_sm[k]);
         for (int w = 0; w < 8; ++w) {
             d.sched[k].base[w] = sched[k].base[w];
             d.sched[k].steps[w] = sched[k].steps[w];

@@ -29,6 +29,7 @@
 struct SchedDev {
     const uint32_t *ctrl;
     const float4 *rec;
+    const uint32_t *gmask;  // [block] groups whose partial-force rows touch the block (W > 1)
     int base[8];   // first step of warp w
     int steps[8];  // steps of warp w
 };
