@@ -506,6 +506,11 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
         }
     }
     if (!GRAD) return team_sum(tm, e, red);
+    // the energy's warp partials go out now, off the critical path; the team
+    // adds them after the gradient's barrier (their slots are rewritten only
+    // after the next evaluation's first barrier)
+    const float ew = warp_sum(e);
+    if (W > 1 && lane == 0) red[16 + tm.warp()] = ew;
     tm.sync();
 
     // Per-atom force = grid part + the partial rows of the groups that
@@ -625,7 +630,15 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
             }
         }
     }
-    return team_sum(tm, e, red);  // its barrier publishes grad[]
+    if (W == 1) {
+        __syncwarp();  // publishes grad[]
+        return ew;
+    }
+    tm.sync();  // publishes grad[] and the energy partials
+    float et = red[16];
+#pragma unroll
+    for (int w = 1; w < W; ++w) et += red[16 + w];
+    return et;
 }
 
 }  // namespace dev

@@ -91,7 +91,7 @@ __host__ __device__ inline EvalLayout eval_layout(int n_atoms, int n_frag, int n
     int o = 0;
     w.geno = o; o += 48 * W;          // a copy per warp
     w.grad = o; o += 48;
-    w.red = o; o += 32;               // two halves of 8 warp partials
+    w.red = o; o += 32;               // team sums: two halves of 8 warp partials, then 8 energy partials
     w.M = o; o += 12 * n_frag * W;    // a copy per warp
     w.fs = o; o += grad ? 8 * n_frag : 0;
     w.x = o; o += 4 * nb8 * W;        // a copy per warp
