@@ -291,6 +291,10 @@ int dock_microbench(dock_ctx *ctx, int what, double *value);
  * server_poll: *done = 1 once all nruns tasks from first_task are finished.
  * server_result: host outputs best_geno [nruns][n_genes], best_E [nruns]
  * (FP64 re-score), evals_used [nruns] (each may be NULL).
+ * server_cancel: withdraws the runs of a submitted request that no warp has
+ * claimed yet (best effort: a run already running finishes normally); a
+ * withdrawn run completes at once with evals_used 0 and best_E = +inf.
+ * Errors: a task range not submitted.
  * server_destroy: asks the warps to leave, waits for them, frees. */
 typedef struct dock_server dock_server;
 int server_create(dock_ctx *ctx, int capacity, int max_atoms, int pop_max, dock_server **out);
@@ -299,6 +303,7 @@ int server_submit(dock_server *srv, const dock_grids *grids, const dock_ligand *
 int server_poll(dock_server *srv, int64_t first_task, int nruns, int *done);
 int server_result(dock_server *srv, int64_t first_task, int nruns, int n_genes, float *best_geno, double *best_E,
                   int64_t *evals_used);
+int server_cancel(dock_server *srv, int64_t first_task, int nruns);
 int server_destroy(dock_server *srv);
 
 /* ---- docking without device allocation ----

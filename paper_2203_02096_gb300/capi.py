@@ -74,6 +74,7 @@ SIGNATURES = {
     "server_poll": (_i, [_vp, _i64, _i, _P(_i)]),
     "server_result": (_i, [_vp, _i64, _i, _i, _vp, _vp, _vp]),
     "server_destroy": (_i, [_vp]),
+    "server_cancel": (_i, [_vp, _i64, _i]),
     "dock_init_population": (_i, [_vp, _vp, _i, _i, _i, _u64, _vp, _vp]),
     "dock_ga_children": (_i, [_vp, _i, _i, _i, _vp, _vp, _u64, _u32, _P(DockParams), _vp, _vp, _vp]),
     "dock_ls_picks": (_i, [_vp, _i, _i, _i, _u64, _u32, _vp, _vp]),
@@ -404,6 +405,10 @@ class Server:
         self.ctx.check(self.ctx.lib.server_result(self.h, int(first_task), int(nruns), int(n_genes), _ptr(g), _ptr(e),
                                                   _ptr(v)), "server_result")
         return g, e, v
+
+    def cancel(self, first_task: int, nruns: int):
+        """Withdraw the request's runs no warp has started (they finish at once, evals 0, energy +inf)."""
+        self.ctx.check(self.ctx.lib.server_cancel(self.h, int(first_task), int(nruns)), "server_cancel")
 
     def close(self):
         if getattr(self, "h", None) is not None and self.ctx.h is not None:

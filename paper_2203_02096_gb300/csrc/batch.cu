@@ -354,6 +354,8 @@ struct ServeTask {
     BatchConst P;
     unsigned long long seed;
     int run, out;
+    int cancel;  // set by server_cancel: the warp that claims the task skips it
+    int pad;
 };
 
 struct ServeCtl {
@@ -456,11 +458,16 @@ lga_serve(const volatile ServeTask *tasks, const volatile ServeCtl *ctl, int cap
         const EvalLayout Yg = eval_layout(L.n_atoms, L.n_frag, L.nb8, true, 1);
         const WarpScratch S = warp_scratch(scratch, floats_per_warp, gw, pop_max, 7 + DOCK_MAX_TORSIONS);
         const int out = T->out;
-        const long long ev = dock_run_warp<-1>(L, G, C, P, ws, Yn, Yg, S, T->run, best_geno + (size_t)out * P.gstride,
-                                               best_E32 + out);
+        // a cancelled task is finished at once: no evaluations, energy +inf
+        const bool cancelled = ((const volatile ServeTask *)(tasks + (t % capacity)))->cancel != 0;
+        long long ev = 0;
+        if (!cancelled)
+            ev = dock_run_warp<-1>(L, G, C, P, ws, Yn, Yg, S, T->run, best_geno + (size_t)out * P.gstride,
+                                   best_E32 + out);
         __syncwarp();
         if (lane == 0) {
-            best_E[out] = rescore64_one(L, G, best_geno + (size_t)out * P.gstride);
+            best_E[out] = cancelled ? __longlong_as_double(0x7ff0000000000000ll)
+                                    : rescore64_one(L, G, best_geno + (size_t)out * P.gstride);
             evals[out] = (unsigned long long)ev;
             __threadfence_system();
             done[out] = t + 1;  // completion: the task's sequence number
@@ -611,6 +618,7 @@ int server_submit(dock_server *S, const dock_grids *grids, const dock_ligand *li
         T.seed = seed;
         T.run = r;
         T.out = (int)(t % S->capacity);
+        T.cancel = 0;
     }
     S->submitted = last + 1;
     __atomic_thread_fence(__ATOMIC_SEQ_CST);
@@ -629,6 +637,18 @@ int server_poll(dock_server *S, int64_t first_task, int nruns, int *done) {
     }
     *done = all;
     if (!all) return server_kick(S);  // keep the kernel alive while work is pending
+    return DOCK_OK;
+}
+
+int server_cancel(dock_server *S, int64_t first_task, int nruns) {
+    if (!S || nruns < 1 || first_task < 0 || first_task + nruns > S->submitted)
+        return S ? set_err(S->ctx, DOCK_ERR_INVALID, "server_cancel: not a submitted task range") : DOCK_ERR_INVALID;
+    for (int r = 0; r < nruns; ++r) {
+        const long long t = first_task + r;
+        if (t < S->submitted - S->capacity) continue;  // its slot was reused: long finished
+        *(volatile int *)&S->tasks[t % S->capacity].cancel = 1;
+    }
+    __atomic_thread_fence(__ATOMIC_SEQ_CST);
     return DOCK_OK;
 }
 

@@ -302,11 +302,13 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
     const int PS = NB + 4;
 
     // Warp 0: rigid-body transform and the torsion tree.  Torsion k is lane
-    // k < 32; its fragment's full transform M_{k+1} = M_0 o L_a o ... o L_k
-    // is built by pointer jumping over the tree: each round composes a
-    // lane's partial product with its current ancestor's and jumps to that
-    // ancestor's ancestor, so depth d takes ceil(log2 d) + 1 rounds of
-    // shuffles instead of d rounds through shared memory.
+    // k < 32; its fragment's full transform M_{k+1} = M_0 o L_a o ... o L_k.
+    // Teams of several warps (the local search, latency-bound) build it by
+    // pointer jumping over the tree: each round composes a lane's partial
+    // product with its current ancestor's (shuffles) and jumps to that
+    // ancestor's ancestor, so depth d takes ceil(log2 d) + 1 rounds.  One-warp
+    // teams go level by level through shared memory (measured faster inside
+    // the serving kernel, equal elsewhere).
     if (tm.warp() == 0) {
         __syncwarp();
         float qw = geno[3], qx = geno[4], qy = geno[5], qz = geno[6];
@@ -358,27 +360,46 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
             r00 = n00; r01 = n01; r02 = n02; r10 = n10; r11 = n11; r12 = n12; r20 = n20; r21 = n21; r22 = n22;
             t0 = m0; t1 = m1; t2 = m2;
         };
-        if (lane < T && up == 0) compose(q00, q01, q02, q10, q11, q12, q20, q21, q22, 0.f, 0.f, 0.f);
-        // at most 6 rounds: depth <= 32 = 2^5
-        for (int jump = 0; jump < 6 && __any_sync(0xffffffffu, lane < T && up != 0); ++jump) {
-            const int src = up > 0 ? up - 1 : lane;  // lane holding fragment `up`
-            const float a00 = __shfl_sync(0xffffffffu, r00, src), a01 = __shfl_sync(0xffffffffu, r01, src);
-            const float a02 = __shfl_sync(0xffffffffu, r02, src), a10 = __shfl_sync(0xffffffffu, r10, src);
-            const float a11 = __shfl_sync(0xffffffffu, r11, src), a12 = __shfl_sync(0xffffffffu, r12, src);
-            const float a20 = __shfl_sync(0xffffffffu, r20, src), a21 = __shfl_sync(0xffffffffu, r21, src);
-            const float a22 = __shfl_sync(0xffffffffu, r22, src), b0 = __shfl_sync(0xffffffffu, t0, src);
-            const float b1 = __shfl_sync(0xffffffffu, t1, src), b2 = __shfl_sync(0xffffffffu, t2, src);
-            const int up2 = __shfl_sync(0xffffffffu, up, src);
-            if (lane < T && up != 0) {
-                compose(a00, a01, a02, a10, a11, a12, a20, a21, a22, b0, b1, b2);
-                up = up2;
+        if (W == 1) {
+            // level by level: M_{k+1} = M_parent o L_k
+            const int depth = lane < T ? ldg(L.frag + lane + 1).w : 0, parent = up;
+            for (int d = 1; d <= L.max_depth; ++d) {
+                __syncwarp();
+                if (lane < T && depth == d) {
+                    const float4 p0 = M[3 * parent], p1 = M[3 * parent + 1], p2 = M[3 * parent + 2];
+                    float4 *o = M + 3 * (lane + 1);
+                    o[0] = make_float4(p0.x * r00 + p0.y * r10 + p0.z * r20, p0.x * r01 + p0.y * r11 + p0.z * r21,
+                                       p0.x * r02 + p0.y * r12 + p0.z * r22, p0.x * t0 + p0.y * t1 + p0.z * t2 + p0.w);
+                    o[1] = make_float4(p1.x * r00 + p1.y * r10 + p1.z * r20, p1.x * r01 + p1.y * r11 + p1.z * r21,
+                                       p1.x * r02 + p1.y * r12 + p1.z * r22, p1.x * t0 + p1.y * t1 + p1.z * t2 + p1.w);
+                    o[2] = make_float4(p2.x * r00 + p2.y * r10 + p2.z * r20, p2.x * r01 + p2.y * r11 + p2.z * r21,
+                                       p2.x * r02 + p2.y * r12 + p2.z * r22, p2.x * t0 + p2.y * t1 + p2.z * t2 + p2.w);
+                }
             }
-        }
-        if (lane < T) {
-            float4 *o = M + 3 * (lane + 1);
-            o[0] = make_float4(r00, r01, r02, t0);
-            o[1] = make_float4(r10, r11, r12, t1);
-            o[2] = make_float4(r20, r21, r22, t2);
+            (void)compose;
+        } else {
+            if (lane < T && up == 0) compose(q00, q01, q02, q10, q11, q12, q20, q21, q22, 0.f, 0.f, 0.f);
+            // at most 6 rounds: depth <= 32 = 2^5
+            for (int jump = 0; jump < 6 && __any_sync(0xffffffffu, lane < T && up != 0); ++jump) {
+                const int src = up > 0 ? up - 1 : lane;  // lane holding fragment `up`
+                const float a00 = __shfl_sync(0xffffffffu, r00, src), a01 = __shfl_sync(0xffffffffu, r01, src);
+                const float a02 = __shfl_sync(0xffffffffu, r02, src), a10 = __shfl_sync(0xffffffffu, r10, src);
+                const float a11 = __shfl_sync(0xffffffffu, r11, src), a12 = __shfl_sync(0xffffffffu, r12, src);
+                const float a20 = __shfl_sync(0xffffffffu, r20, src), a21 = __shfl_sync(0xffffffffu, r21, src);
+                const float a22 = __shfl_sync(0xffffffffu, r22, src), b0 = __shfl_sync(0xffffffffu, t0, src);
+                const float b1 = __shfl_sync(0xffffffffu, t1, src), b2 = __shfl_sync(0xffffffffu, t2, src);
+                const int up2 = __shfl_sync(0xffffffffu, up, src);
+                if (lane < T && up != 0) {
+                    compose(a00, a01, a02, a10, a11, a12, a20, a21, a22, b0, b1, b2);
+                    up = up2;
+                }
+            }
+            if (lane < T) {
+                float4 *o = M + 3 * (lane + 1);
+                o[0] = make_float4(r00, r01, r02, t0);
+                o[1] = make_float4(r10, r11, r12, t1);
+                o[2] = make_float4(r20, r21, r22, t2);
+            }
         }
     }
     // Force accumulators start at zero: W = 1 adds pair forces straight into
