@@ -69,7 +69,7 @@ struct Team {
 // Where an atom sits in the grid: cell index, in-cell fractions, clamping
 // and the out-of-box penalty (energy and its gradient in kcal/mol/A).
 struct CellPos {
-    int cell;
+    long long cell;  // quad index of the cell's lower z plane within a map
     float fx, fy, fz;
     bool cx, cy, cz;
     float pen, gpx, gpy, gpz;
@@ -96,18 +96,13 @@ __device__ __forceinline__ void locate(const GridDev &G, float ux, float uy, flo
     clamp_axis(ux, G.nx, G.h, ix, c.fx, c.cx, c.pen, c.gpx);
     clamp_axis(uy, G.ny, G.h, iy, c.fy, c.cy, c.pen, c.gpy);
     clamp_axis(uz, G.nz, G.h, iz, c.fz, c.cz, c.pen, c.gpz);
-    c.cell = (iz * (G.ny - 1) + iy) * (G.nx - 1) + ix;
+    c.cell = ((long long)iy * (G.nx - 1) + ix) * G.nz + iz;
 }
 
-// The 8 corner values of map m in the located cell (one 32-byte sector).
+// The 8 corner values of map m in the located cell: quads iz and iz + 1.
 struct Cell8 {
     float4 a, b;
 };
-
-__device__ __forceinline__ Cell8 load_cell(const GridDev &G, int cell, int m) {
-    const float4 *p = G.cells + 2 * ((size_t)cell * G.M + m);
-    return Cell8{ldg(p), ldg(p + 1)};
-}
 
 // Trilinear read in the located cell; derivatives are with respect to the
 // in-cell fractions.
@@ -151,13 +146,15 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 __device__ __forceinline__ void atom_stage(const GridDev &G, int map_t, float ux, float uy, float uz, float4 *dst) {
     CellPos c;
     locate(G, ux, uy, uz, c);
-    const float4 *b = G.cells + 2 * ((size_t)c.cell * G.M);
-    cp_async16(dst + 0, b + 2 * map_t);
-    cp_async16(dst + 1, b + 2 * map_t + 1);
-    cp_async16(dst + 2, b + 2 * G.emap);
-    cp_async16(dst + 3, b + 2 * G.emap + 1);
-    cp_async16(dst + 4, b + 2 * G.dmap);
-    cp_async16(dst + 5, b + 2 * G.dmap + 1);
+    const float4 *bt = G.cells + (size_t)map_t * G.mstride + c.cell;
+    const float4 *be = G.cells + (size_t)G.emap * G.mstride + c.cell;
+    const float4 *bd = G.cells + (size_t)G.dmap * G.mstride + c.cell;
+    cp_async16(dst + 0, bt);
+    cp_async16(dst + 1, bt + 1);
+    cp_async16(dst + 2, be);
+    cp_async16(dst + 3, be + 1);
+    cp_async16(dst + 4, bd);
+    cp_async16(dst + 5, bd + 1);
 }
 
 // The staged cells of an atom back as AtomCells (its cell position located

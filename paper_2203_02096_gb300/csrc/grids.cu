@@ -9,17 +9,15 @@ namespace {
 // Cell-major copy: thread per (cell, map), 8 corner values -> 2 float4.
 __global__ void relayout_kernel(const float *__restrict__ nodes, int nx, int ny, int nz, int M, float4 *cells) {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long ncell = (long long)(nx - 1) * (ny - 1) * (nz - 1);
-    if (idx >= ncell * M) return;
-    const long long cell = idx / M;
-    const int m = (int)(idx % M);
-    const int ix = (int)(cell % (nx - 1));
-    const int iy = (int)((cell / (nx - 1)) % (ny - 1));
-    const int iz = (int)(cell / ((long long)(nx - 1) * (ny - 1)));
+    const long long ncol = (long long)(nx - 1) * (ny - 1);
+    if (idx >= ncol * nz * M) return;
+    const int iz = (int)(idx % nz);
+    const long long col = (idx / nz) % ncol;
+    const int m = (int)(idx / (nz * ncol));
+    const int ix = (int)(col % (nx - 1)), iy = (int)(col / (nx - 1));
     const size_t plane = (size_t)nx * ny;
     const float *b = nodes + (size_t)m * plane * nz + (size_t)iz * plane + (size_t)iy * nx + ix;
-    cells[2 * idx] = make_float4(b[0], b[1], b[nx], b[nx + 1]);
-    cells[2 * idx + 1] = make_float4(b[plane], b[plane + 1], b[plane + nx], b[plane + nx + 1]);
+    cells[idx] = make_float4(b[0], b[1], b[nx], b[nx + 1]);
 }
 
 struct MapConst {
@@ -89,7 +87,7 @@ build_maps_kernel(int n_rec, const float4 *__restrict__ rec, const int *__restri
 }  // namespace
 
 cudaError_t launch_relayout(const GridDev &g, float4 *cells, cudaStream_t s) {
-    const long long n = (long long)(g.nx - 1) * (g.ny - 1) * (g.nz - 1) * g.M;
+    const long long n = (long long)(g.nx - 1) * (g.ny - 1) * g.nz * g.M;
     relayout_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g.nodes, g.nx, g.ny, g.nz, g.M, cells);
     return cudaGetLastError();
 }

@@ -265,8 +265,8 @@ static int finish_grids(dock_ctx *ctx, dock_grids *g, const int dims[3], const d
         else if (t == DOCK_MAP_DESOLV) d.dmap = m;
         else g->map_of_type[t] = m;
     }
-    const size_t ncell = (size_t)(d.nx - 1) * (d.ny - 1) * (d.nz - 1);
-    g->cells_mem = dev_alloc(ctx, ncell * d.M * 32, s);
+    d.mstride = (long long)(d.nx - 1) * (d.ny - 1) * d.nz;
+    g->cells_mem = dev_alloc(ctx, (size_t)d.mstride * d.M * 16, s);
     g->lut_mem = dev_alloc(ctx, 8 * sizeof(int), s);
     if (!g->cells_mem || !g->lut_mem) return set_err(ctx, DOCK_ERR_OOM, "grid allocation failed");
     d.cells = (const float4 *)g->cells_mem;

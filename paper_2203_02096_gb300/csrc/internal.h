@@ -62,12 +62,15 @@ struct LigandDev {
     const double *q64;        // [n] charges (FP64 re-score)
 };
 
-// Receptor grids on the device.  cells: cell-major copy, for cell
-// c = (iz*(ny-1) + iy)*(nx-1) + ix and map m the 8 corner values at
-// float4 index 2*(c*M + m): (v000, v100, v010, v110), (v001, v101, v011, v111)
-// (corner bits x, y, z), so one atom-map read is one 32-byte sector.
+// Receptor grids on the device.  cells: z-column quad copy.  For map m,
+// column (ix, iy) (ix < nx-1, iy < ny-1) and node plane iz < nz, the quad
+// (v(ix,iy,iz), v(ix+1,iy,iz), v(ix,iy+1,iz), v(ix+1,iy+1,iz)) is float4
+// number m*mstride + (iy*(nx-1) + ix)*nz + iz, mstride = (nx-1)(ny-1)nz.
+// A cell's 8 corners are two adjacent quads (iz, iz+1): one 32-byte read,
+// 4x the node-major size (a full cell-major copy would be 8x).
 struct GridDev {
     const float4 *cells;
+    long long mstride;        // quads per map
     const float *nodes;       // [M][nz][ny][nx] node-major copy
     const int *map_of_type;   // [8] ligand type -> map, -1 if absent
     int nx, ny, nz, M;

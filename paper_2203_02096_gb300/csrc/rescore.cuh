@@ -22,8 +22,8 @@ __device__ double interp64(const GridDev &G, int m, const double *u, double &pen
         const double dh = d * G.h64;
         pen += 10.0 * dh * dh;
     }
-    const int cell = (i0[2] * (G.ny - 1) + i0[1]) * (G.nx - 1) + i0[0];
-    const float4 a = G.cells[2 * ((size_t)cell * G.M + m)], b = G.cells[2 * ((size_t)cell * G.M + m) + 1];
+    const long long q = (size_t)m * G.mstride + ((long long)i0[1] * (G.nx - 1) + i0[0]) * G.nz + i0[2];
+    const float4 a = G.cells[q], b = G.cells[q + 1];
     const double v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
     double s = 0.0;
     for (int c = 0; c < 8; ++c) {
