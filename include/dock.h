@@ -164,7 +164,7 @@ int free_ligand(dock_ctx *ctx, dock_ligand *lig);
 /* Device bytes a loaded ligand holds (for admission by device memory). */
 int ligand_device_bytes(const dock_ligand *lig, size_t *bytes);
 
-/* ---- batched evaluation (spec: score_batch, score_grad_batch) ----
+/* ---- batched evaluation of genotypes (paper, Section II-A: population-parallel pose evaluation) ----
  * geno: device [B][G] FP32.  E: device [B] FP32 energies (kcal/mol).
  * grad: device [B][G] FP32, dE/dgenotype (the quaternion part is the
  * derivative through the normalisation, so it is orthogonal to q).
