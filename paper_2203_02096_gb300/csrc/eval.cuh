@@ -288,12 +288,6 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
     float4 *PF = reinterpret_cast<float4 *>(ws + Y.pf);
     float *red = ws + Y.red;
     const int T = L.n_tors, N = L.n_atoms, NB = L.nb8;
-    // the per-atom grid phase gives each warp a contiguous run of ceil(N/W)
-    // atoms (an even split whose lanes touch consecutive float4 in shared
-    // memory, free of bank conflicts): this thread's atoms are i0, i0 + 32, ...
-    // below i1
-    const int chunk = (N + W - 1) / W;
-    const int i0 = tm.warp() * chunk + lane, i1 = min(N, (tm.warp() + 1) * chunk);
     // partial-force rows of the W > 1 groups: NB + 4 float4 apart, so the two
     // rows a quarter-warp reads at once fall on different banks
     const int PS = NB + 4;
@@ -410,33 +404,29 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
     }
     tm.sync();
 
-    // Atom positions relative to t (padding atoms up to a multiple of 8 at 0).
+    // Atom positions relative to t (padding atoms up to a multiple of 8 at
+    // 0).  The thread that places an atom also sends out the reads of its
+    // three map cells, staged into shared memory asynchronously: they are in
+    // flight through the pair rounds, and the same thread reads them back
+    // (consecutive atoms on consecutive lanes).
+    const float tux = (geno[0] - G.ox) * G.inv_h, tuy = (geno[1] - G.oy) * G.inv_h, tuz = (geno[2] - G.oz) * G.inv_h;
+    float4 *Cst = reinterpret_cast<float4 *>(ws + Y.cst);
     for (int i = r; i < NB; i += S) {
         float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
         if (i < N) {
             const float4 p = ldg(L.ref + i);
-            const int f = ldg(L.meta + i) >> 8;
+            const int meta = ldg(L.meta + i), f = meta >> 8;
             const float4 m0 = M[3 * f], m1 = M[3 * f + 1], m2 = M[3 * f + 2];
             x = make_float4(fmaf(m0.x, p.x, fmaf(m0.y, p.y, fmaf(m0.z, p.z, m0.w))),
                             fmaf(m1.x, p.x, fmaf(m1.y, p.y, fmaf(m1.z, p.z, m1.w))),
                             fmaf(m2.x, p.x, fmaf(m2.y, p.y, fmaf(m2.z, p.z, m2.w))), 0.f);
+            atom_stage(G, ldg(G.map_of_type + (meta & 255)), fmaf(x.x, G.inv_h, tux), fmaf(x.y, G.inv_h, tuy),
+                       fmaf(x.z, G.inv_h, tuz), Cst + 6 * i);
         }
         X[i] = x;
     }
-    tm.sync();
-
-    // Particle-grid reads of the thread's atoms go out first, staged into
-    // shared memory asynchronously; the pair rounds run while they are in
-    // flight.
-    const float tx = geno[0], ty = geno[1], tz = geno[2];
-    const float tux = (tx - G.ox) * G.inv_h, tuy = (ty - G.oy) * G.inv_h, tuz = (tz - G.oz) * G.inv_h;
-    float4 *Cst = reinterpret_cast<float4 *>(ws + Y.cst);
-    for (int i = i0; i < i1; i += 32) {
-        const float4 xi = X[i];
-        atom_stage(G, ldg(G.map_of_type + (ldg(L.meta + i) & 255)), fmaf(xi.x, G.inv_h, tux),
-                   fmaf(xi.y, G.inv_h, tuy), fmaf(xi.z, G.inv_h, tuz), Cst + 6 * i);
-    }
     cp_async_commit();
+    tm.sync();
 
     // Intramolecular pairs, systolic: in a step, lane l of group q holds its
     // own atom of block A and, passed one lane along per round, the force
@@ -504,9 +494,17 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
             if (GRAD && W == 1) __syncwarp();
         }
     }
-    if (W == 1 && GRAD) __syncwarp();  // pair forces in Fv before the grid part is added
+    // pair forces complete: W = 1 in Fv, W > 1 in every group's partials
+    if (GRAD) tm.sync();
     cp_async_wait_all();
-    for (int i = i0; i < i1; i += 32) {
+
+    // Per atom: grid energy and force from the staged cells, the complete
+    // force (W = 1: the pair force in Fv plus the grid part; W > 1: the grid
+    // part plus the partial rows of the groups whose steps touched the atom's
+    // block, ascending group order) and the torque (x_i - t) x f_i.
+    float4 *Tq = reinterpret_cast<float4 *>(ws + Y.tq);
+    const uint32_t *gmask = L.sched[W == 1 ? 0 : W == 2 ? 1 : W == 4 ? 2 : 3].gmask;
+    for (int i = r; i < N; i += S) {
         const float4 xi = X[i];
         AtomCells A0;
         atom_unstage(G, ldg(L.ref + i).w, fmaf(xi.x, G.inv_h, tux), fmaf(xi.y, G.inv_h, tuy),
@@ -514,13 +512,22 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
         float3 g;
         e += atom_grid_energy<GRAD>(G, A0, g);
         if (GRAD) {
+            float fx, fy, fz;
             if (W == 1) {
-                float4 f = Fv[i];
-                f.x += g.x; f.y += g.y; f.z += g.z;
-                Fv[i] = f;
+                const float4 pf = Fv[i];
+                fx = pf.x + g.x; fy = pf.y + g.y; fz = pf.z + g.z;
             } else {
-                Fv[i] = make_float4(g.x, g.y, g.z, 0.f);
+                const uint32_t m = ldg(gmask + (i >> 3));
+                fx = g.x; fy = g.y; fz = g.z;
+#pragma unroll
+                for (int q = 0; q < 4 * W; ++q)
+                    if (m & (1u << q)) {
+                        const float4 v = PF[q * PS + i];
+                        fx += v.x; fy += v.y; fz += v.z;
+                    }
             }
+            Fv[i] = make_float4(fx, fy, fz, 0.f);
+            Tq[i] = make_float4(xi.y * fz - xi.z * fy, xi.z * fx - xi.x * fz, xi.x * fy - xi.y * fx, 0.f);
         }
     }
     if (!GRAD) return team_sum(tm, e, red);
@@ -529,35 +536,6 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
     // after the next evaluation's first barrier)
     const float ew = warp_sum(e);
     if (W > 1 && lane == 0) red[16 + tm.warp()] = ew;
-    tm.sync();
-
-    // Per-atom force = grid part + the partial rows of the groups that
-    // touched the atom's block; torque (x_i - t) x f_i.  W = 1: the forces
-    // are complete already.
-    float4 *Tq = reinterpret_cast<float4 *>(ws + Y.tq);
-    if (W == 1) {
-        for (int i = r; i < N; i += S) {
-            const float4 f = Fv[i], xi = X[i];
-            Tq[i] = make_float4(xi.y * f.z - xi.z * f.y, xi.z * f.x - xi.x * f.z, xi.x * f.y - xi.y * f.x, 0.f);
-        }
-    } else {
-        // atom i sums the partial rows of the groups whose steps touched its
-        // block (ascending group order), then adds its grid force
-        const uint32_t *gmask = L.sched[W == 2 ? 1 : W == 4 ? 2 : 3].gmask;
-        for (int i = r; i < N; i += S) {
-            uint32_t m = ldg(gmask + (i >> 3));
-            const float4 gr = Fv[i], xi = X[i];
-            float fx = gr.x, fy = gr.y, fz = gr.z;
-            while (m) {
-                const int g = __ffs(m) - 1;
-                m &= m - 1;
-                const float4 v = PF[g * PS + i];
-                fx += v.x; fy += v.y; fz += v.z;
-            }
-            Fv[i] = make_float4(fx, fy, fz, 0.f);
-            Tq[i] = make_float4(xi.y * fz - xi.z * fy, xi.z * fx - xi.x * fz, xi.x * fy - xi.y * fx, 0.f);
-        }
-    }
     tm.sync();
 
     // Gradient.  W = 1: per-fragment sums first, then torsion k sums the
@@ -611,6 +589,7 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
                 }
             }
             float a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0, a5 = 0;
+#pragma unroll 4
             for (int j = lo + sub; j < hi; j += m) {
                 const float4 u = W == 1 ? FS[2 * j] : Fv[j], v = W == 1 ? FS[2 * j + 1] : Tq[j];
                 a0 += u.x; a1 += u.y; a2 += u.z;
