@@ -51,6 +51,22 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return y;
 }
 
+// Paired FP32 arithmetic (sm_100-family add/mul/fma .f32x2 through the
+// __fadd2_rn / __fmul2_rn / __ffma2_rn intrinsics): one issue slot for two
+// operations, each rounded like its scalar _rn form.  A paired product that
+// feeds a paired add can still be fused by the code generator in some
+// kernels and not in others, so results would depend on the kernel: the
+// evaluator never adds a paired product with add2 -- products enter sums only
+// through explicit fma2/fmaf or after scalar rounding (__fadd_rn).
+typedef float2 f32x2;
+__device__ __forceinline__ f32x2 pk2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ f32x2 dup2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) { return __ffma2_rn(a, b, c); }
+// a - b as fma(b, -1, a): the same single rounding
+__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+
 // W warps evaluating one genotype.  W = 1: a warp, possibly one of several
 // independent teams in a block; W > 1: the whole block is the team.
 template <int W>
@@ -186,39 +202,53 @@ __device__ __forceinline__ float atom_grid_energy(const GridDev &G, const AtomCe
     return fmaf(aq, vd, fmaf(q, ve, vt)) + A.c.pen;
 }
 
-// Intramolecular pair: energy, and s = (dE/dr)/r (0 below the floor).
-// c = (c12, cn, qq, ds): vdW pairs carry cn = c6 >= 0 (E = c12/r^12 -
-// c6/r^6), H-bond pairs cn = -c10 < 0 (E = c12/r^12 - c10/r^10);
-// qq = w_el 332.06 q_i q_j; ds = w_ds (S_i V_j + S_j V_i).
+// Intramolecular pair energies of two pairs at once (a lane's rounds d and
+// d + 1).  Per pair, with coefficients (c12, cn, qq, ds): vdW pairs carry
+// cn = c6 >= 0 (E = c12/r^12 - c6/r^6), H-bond pairs cn = -c10 < 0 (E =
+// c12/r^12 - c10/r^10); qq = w_el 332.06 q_i q_j; ds = w_ds (S_i V_j + S_j
+// V_i).  r2a, r2b: squared distances; C, N, Q, D: the two pairs' c12, cn, qq,
+// ds.  Returns both energies; with GRAD, sa, sb = (dE/dr)/r (0 below the
+// floor).
 template <bool GRAD>
-__device__ __forceinline__ float pair_energy(float r2, float4 c, float &s) {
-    const float r2e = fmaxf(r2, kFloor2);
-    const float rinv = rsqrtf(r2e);
-    const float r = r2e * rinv;
-    const float ri2 = rinv * rinv, ri6 = ri2 * ri2 * ri2, ri12 = ri6 * ri6;
-    const bool hb = c.y < 0.f;
-    const float rk = hb ? ri6 * ri2 * ri2 : ri6;  // r^-10 or r^-6
-    const float cn = fabsf(c.y);
-    const float ev = fmaf(c.x, ri12, -cn * rk);
+__device__ __forceinline__ f32x2 pair_energy2(float r2a, float r2b, f32x2 C, f32x2 N, f32x2 Q, f32x2 D, float &sa,
+                                              float &sb) {
+    const float r2ea = fmaxf(r2a, kFloor2), r2eb = fmaxf(r2b, kFloor2);
+    const f32x2 R2E = pk2(r2ea, r2eb), RI = pk2(rsqrtf(r2ea), rsqrtf(r2eb));
+    const f32x2 R = mul2(R2E, RI);
+    const f32x2 RI2 = mul2(RI, RI), RI4 = mul2(RI2, RI2), RI6 = mul2(RI4, RI2), RI12 = mul2(RI6, RI6);
+    const f32x2 RI10 = mul2(RI6, RI4);
+    const float na = N.x, nb = N.y, r6a = RI6.x, r6b = RI6.y, r10a = RI10.x, r10b = RI10.y;
+    const bool hba = na < 0.f, hbb = nb < 0.f;
+    const f32x2 RK = pk2(hba ? r10a : r6a, hbb ? r10b : r6b);  // r^-10 or r^-6
+    const f32x2 NCN = pk2(-fabsf(na), -fabsf(nb));
+    const f32x2 EV = fma2(C, RI12, mul2(NCN, RK));
     // sigmoidal dielectric eps = A + B / den, den = 1 + k exp(-lambda B r):
     // eps = D / den with D = A den + B, so one reciprocal rr = 1 / (den D)
     // gives 1/eps = den^2 rr and eps'/eps = B k lambda B e rr
-    const float ex = ex2_approx(-kDielLB2 * r);
-    const float den = fmaf(kDielK, ex, 1.f);
-    const float rr = rcp_approx(den * fmaf(kDielA, den, kDielB));
-    const float inv_eps = (den * den) * rr;
-    // products rounded on their own (never fused into the sum below), so the
-    // energy has the same bits with and without the gradient
-    const float eel = __fmul_rn(__fmul_rn(c.z, rinv), inv_eps);
-    const float eds = __fmul_rn(c.w, ex2_approx(-r2e * kHalfInvSig2L2));
+    const f32x2 T = mul2(R, dup2(-kDielLB2));
+    const f32x2 EX = pk2(ex2_approx(T.x), ex2_approx(T.y));
+    const f32x2 DEN = fma2(dup2(kDielK), EX, dup2(1.f));
+    const f32x2 DD = mul2(DEN, fma2(dup2(kDielA), DEN, dup2(kDielB)));
+    const f32x2 RR = pk2(rcp_approx(DD.x), rcp_approx(DD.y));
+    const f32x2 INV_EPS = mul2(mul2(DEN, DEN), RR);
+    // every product rounded on its own (paired instructions are never
+    // contracted), so an energy has the same bits with and without the
+    // gradient
+    const f32x2 EEL = mul2(mul2(Q, RI), INV_EPS);
+    const f32x2 U = mul2(R2E, dup2(-kHalfInvSig2L2));
+    const f32x2 EDS = mul2(D, pk2(ex2_approx(U.x), ex2_approx(U.y)));
     if (GRAD) {
-        const float dv = fmaf(-12.f * c.x, ri12, (hb ? 10.f : 6.f) * cn * rk) * rinv;
-        const float deps_eps = kDielDeps * ex * rr;
-        const float del = -eel * (rinv + deps_eps);  // d(qq / (eps r)) / dr
-        const float dds = -eds * r * kInvSig2;
-        s = r2 >= kFloor2 ? (dv + del + dds) * rinv : 0.f;
+        // dE/dr = dv - eel (1/r + eps'/eps) - eds r / sigma^2, the last two
+        // terms fused into the sum
+        const f32x2 KN = pk2(hba ? -10.f : -6.f, hbb ? -10.f : -6.f);
+        const f32x2 DV = mul2(fma2(mul2(C, dup2(-12.f)), RI12, mul2(mul2(KN, NCN), RK)), RI);
+        const f32x2 Y = fma2(mul2(dup2(kDielDeps), EX), RR, RI);  // 1/r + eps'/eps
+        const f32x2 T = fma2(mul2(EDS, R), dup2(-kInvSig2), fma2(mul2(EEL, dup2(-1.f)), Y, DV));
+        const f32x2 SS = mul2(T, RI);
+        sa = r2a >= kFloor2 ? SS.x : 0.f;
+        sb = r2b >= kFloor2 ? SS.y : 0.f;
     }
-    return __fadd_rn(__fadd_rn(ev, eel), eds);
+    return pk2(__fadd_rn(__fadd_rn(EV.x, EEL.x), EDS.x), __fadd_rn(__fadd_rn(EV.y, EEL.y), EDS.y));
 }
 
 __device__ __forceinline__ float warp_sum(float v) {
@@ -284,7 +314,15 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
     const int r = tm.rank, lane = tm.lane();
     const float *geno = ws + Y.geno;
     float4 *M = reinterpret_cast<float4 *>(ws + Y.M);
-    float4 *X = reinterpret_cast<float4 *>(ws + Y.x);
+    // atom positions, pair-major: XP[j] = (x_j, x_j', y_j, y_j'), ZP[j] =
+    // (z_j, z_j'), j' = the next atom of j's block (cyclic), so that a lane's
+    // partners of rounds d and d + 1 come in one read as ready pairs
+    float4 *XP = reinterpret_cast<float4 *>(ws + Y.x);
+    float2 *ZP = reinterpret_cast<float2 *>(ws + Y.z);
+    auto pos = [&](int i) {
+        const float4 v = XP[i];
+        return make_float3(v.x, v.z, ZP[i].x);
+    };
     float4 *PF = reinterpret_cast<float4 *>(ws + Y.pf);
     float *red = ws + Y.red;
     const int T = L.n_tors, N = L.n_atoms, NB = L.nb8;
@@ -423,7 +461,14 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
             atom_stage(G, ldg(G.map_of_type + (meta & 255)), fmaf(x.x, G.inv_h, tux), fmaf(x.y, G.inv_h, tuy),
                        fmaf(x.z, G.inv_h, tuz), Cst + 6 * i);
         }
-        X[i] = x;
+        float *xp = reinterpret_cast<float *>(XP), *zp = reinterpret_cast<float *>(ZP);
+        const int prev = (i & ~7) | ((i + 7) & 7);
+        xp[4 * i] = x.x;
+        xp[4 * i + 2] = x.y;
+        zp[2 * i] = x.z;
+        xp[4 * prev + 1] = x.x;
+        xp[4 * prev + 3] = x.y;
+        zp[2 * prev + 1] = x.z;
     }
     cp_async_commit();
     tm.sync();
@@ -432,6 +477,7 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
     // own atom of block A and, passed one lane along per round, the force
     // owed to the atom of block B it meets; after 8 rounds that force is back
     // at the lane owning the B atom, and both go to the group's partials.
+    // Rounds go two at a time in paired FP32 instructions.
     float e = 0.f;
     {
         const SchedDev &SD = L.sched[W == 1 ? 0 : W == 2 ? 1 : W == 4 ? 2 : 3];
@@ -439,39 +485,58 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
         const int nxt = gb | ((sl + 1) & 7);
         float4 *pq = W == 1 ? Fv : PF + q * PS;  // W = 1: the step's groups touch disjoint atoms
         const int s0 = SD.base[w], s1 = s0 + SD.steps[w];
-        // one round: the pair (own atom, atom 8B + (sl + d) mod 8) with
-        // coefficients c; the force owed to the B atom travels one lane on
-        auto round = [&](const float4 &xa, int B, int d, const float4 &c, float &ax, float &ay, float &az, float &bx,
-                         float &by, float &bz) {
-            const float4 xb = X[8 * B + ((sl + d) & 7)];
-            const float ddx = xa.x - xb.x, ddy = xa.y - xb.y, ddz = xa.z - xb.z;
-            const float r2 = fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz));
+        f32x2 E2 = dup2(0.f);  // energies of even and odd rounds
+        // rounds d and d + 1: the pairs (own atom, atoms 8B + (sl + d) mod 8
+        // and the next), coefficients from the records at rq; the force owed
+        // to the B atom travels one lane on after each round
+        auto round2 = [&](f32x2 XA, f32x2 YA, f32x2 ZA, int B, int d, const float4 *rq, f32x2 &AX, f32x2 &AY,
+                          f32x2 &AZ, float &bx, float &by, float &bz) {
+            const int j = 8 * B + ((sl + d) & 7);
+            const float4 pxy = XP[j];
+            const float2 pz = ZP[j];
+            const f32x2 PX = pk2(pxy.x, pxy.y), PY = pk2(pxy.z, pxy.w), PZ = pk2(pz.x, pz.y);
+            const float4 cn4 = ldg(rq), qd4 = ldg(rq + 32);
+            const f32x2 C = pk2(cn4.x, cn4.y), N = pk2(cn4.z, cn4.w), Q = pk2(qd4.x, qd4.y), D = pk2(qd4.z, qd4.w);
+            const f32x2 DX = sub2(XA, PX), DY = sub2(YA, PY), DZ = sub2(ZA, PZ);
+            const f32x2 R2 = fma2(DX, DX, fma2(DY, DY, mul2(DZ, DZ)));
+            const float r2a = R2.x, r2b = R2.y;
             // every round computes; the cutoff selects (one basic block for
             // all rounds, so they overlap)
-            float s;
-            const float ep = pair_energy<GRAD>(r2, c, s);
-            const bool in = r2 < kCut2;
-            e += in ? ep : 0.f;
+            float sa = 0.f, sb = 0.f;
+            const f32x2 EP = pair_energy2<GRAD>(r2a, r2b, C, N, Q, D, sa, sb);
+            const float ea = EP.x, eb = EP.y;
+            const bool ina = r2a < kCut2, inb = r2b < kCut2;
+            E2 = add2(E2, pk2(ina ? ea : 0.f, inb ? eb : 0.f));
             if (GRAD) {
-                s = in ? s : 0.f;
-                const float fx = s * ddx, fy = s * ddy, fz = s * ddz;
-                ax += fx; ay += fy; az += fz;
-                bx = __shfl_sync(0xffffffffu, bx - fx, nxt);
-                by = __shfl_sync(0xffffffffu, by - fy, nxt);
-                bz = __shfl_sync(0xffffffffu, bz - fz, nxt);
+                // force s d on the own atom, -s d on the partner (fused)
+                const float s0 = ina ? sa : 0.f, s1 = inb ? sb : 0.f;
+                const f32x2 S2 = pk2(s0, s1);
+                AX = fma2(S2, DX, AX);
+                AY = fma2(S2, DY, AY);
+                AZ = fma2(S2, DZ, AZ);
+                bx = __shfl_sync(0xffffffffu, fmaf(-s0, DX.x, bx), nxt);
+                by = __shfl_sync(0xffffffffu, fmaf(-s0, DY.x, by), nxt);
+                bz = __shfl_sync(0xffffffffu, fmaf(-s0, DZ.x, bz), nxt);
+                bx = __shfl_sync(0xffffffffu, fmaf(-s1, DX.y, bx), nxt);
+                by = __shfl_sync(0xffffffffu, fmaf(-s1, DY.y, by), nxt);
+                bz = __shfl_sync(0xffffffffu, fmaf(-s1, DZ.y, bz), nxt);
             }
         };
         for (int st = s0; st < s1; ++st) {
             const uint32_t ctl = ldg(SD.ctrl + 4 * st + (lane >> 3));
             const int A = SCH_A(ctl), B = SCH_B(ctl);
-            const float4 xa = X[8 * A + sl];
+            const float3 xa = pos(8 * A + sl);
+            const f32x2 XA = dup2(xa.x), YA = dup2(xa.y), ZA = dup2(xa.z);
+            // records of round pair p: rec[st][p][0][lane] = (c12, c12', cn,
+            // cn'), rec[st][p][1][lane] = (qq, qq', ds, ds')
             const float4 *rp = SD.rec + 256 * (size_t)st + lane;
-            float ax = 0.f, ay = 0.f, az = 0.f, bx = 0.f, by = 0.f, bz = 0.f;
+            f32x2 AX = dup2(0.f), AY = dup2(0.f), AZ = dup2(0.f);
+            float bx = 0.f, by = 0.f, bz = 0.f;
             if (W == 1 && (ctl & SCH_HALF)) {
                 // diagonal blocks, rounds 1-4: the travelling force ends 4
                 // lanes on; the atom's owner fetches it from lane sl + 3
-#pragma unroll
-                for (int d = 1; d <= 4; ++d) round(xa, B, d, ldg(rp + 32 * d), ax, ay, az, bx, by, bz);
+                round2(XA, YA, ZA, B, 1, rp, AX, AY, AZ, bx, by, bz);
+                round2(XA, YA, ZA, B, 3, rp + 64, AX, AY, AZ, bx, by, bz);
                 if (GRAD) {
                     const int src = gb | ((sl + 3) & 7);
                     bx = __shfl_sync(0xffffffffu, bx, src);
@@ -480,11 +545,13 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
                 }
             } else {
 #pragma unroll
-                for (int d = 0; d < 8; ++d) round(xa, B, d, ldg(rp + 32 * d), ax, ay, az, bx, by, bz);
+                for (int p = 0; p < 4; ++p) round2(XA, YA, ZA, B, 2 * p, rp + 64 * p, AX, AY, AZ, bx, by, bz);
             }
             if (GRAD && (ctl & SCH_VALID)) {
                 float4 pa = pq[8 * A + sl];
-                pa.x += ax; pa.y += ay; pa.z += az;
+                pa.x += AX.x + AX.y;
+                pa.y += AY.x + AY.y;
+                pa.z += AZ.x + AZ.y;
                 pq[8 * A + sl] = pa;  // (a diagonal block's second update below is this thread's too)
                 float4 pb = pq[8 * B + sl];
                 pb.x += bx; pb.y += by; pb.z += bz;
@@ -493,6 +560,7 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
             // W = 1: the next step may give these atoms to another group
             if (GRAD && W == 1) __syncwarp();
         }
+        e = E2.x + E2.y;
     }
     // pair forces complete: W = 1 in Fv, W > 1 in every group's partials
     if (GRAD) tm.sync();
@@ -505,7 +573,7 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
     float4 *Tq = reinterpret_cast<float4 *>(ws + Y.tq);
     const uint32_t *gmask = L.sched[W == 1 ? 0 : W == 2 ? 1 : W == 4 ? 2 : 3].gmask;
     for (int i = r; i < N; i += S) {
-        const float4 xi = X[i];
+        const float3 xi = pos(i);
         AtomCells A0;
         atom_unstage(G, ldg(L.ref + i).w, fmaf(xi.x, G.inv_h, tux), fmaf(xi.y, G.inv_h, tuy),
                      fmaf(xi.z, G.inv_h, tuz), Cst + 6 * i, A0);
@@ -599,7 +667,7 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
             if (act && sub == 0) {
                 if (k < T) {  // u_k . sum over the moved atoms of (x_i - x_b) x f_i
                     const int2 ab = ldg(L.tors_ab + k);
-                    const float4 xa = X[ab.x], xb = X[ab.y];
+                    const float3 xa = pos(ab.x), xb = pos(ab.y);
                     float ux = xb.x - xa.x, uy = xb.y - xa.y, uz = xb.z - xa.z;
                     const float il = rsqrtf(fmaf(ux, ux, fmaf(uy, uy, uz * uz)));
                     ux *= il; uy *= il; uz *= il;

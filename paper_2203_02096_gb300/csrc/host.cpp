@@ -553,6 +553,21 @@ SchedHost build_sched(int n, int W, const std::vector<int> &pidx, const std::vec
                     }
             }
         }
+    // by round pair for the paired FP32 rounds: rounds (2p, 2p + 1), or (2p +
+    // 1, 2p + 2) in a half step
+    std::vector<float4> by_round = std::move(S.rec);
+    S.rec.assign(ns * 256, make_float4(0.f, 0.f, 0.f, 0.f));
+    for (size_t st = 0; st < ns; ++st) {
+        const bool hs = (S.ctrl[4 * st] & SCH_HALF) != 0;
+        for (int p = 0; p < (hs ? 2 : 4); ++p) {
+            const int d0 = hs ? 2 * p + 1 : 2 * p;
+            for (int lane = 0; lane < 32; ++lane) {
+                const float4 c0 = by_round[256 * st + 32 * d0 + lane], c1 = by_round[256 * st + 32 * (d0 + 1) + lane];
+                S.rec[256 * st + 64 * p + lane] = make_float4(c0.x, c1.x, c0.y, c1.y);
+                S.rec[256 * st + 64 * p + 32 + lane] = make_float4(c0.z, c1.z, c0.w, c1.w);
+            }
+        }
+    }
     return S;
 }
 

@@ -23,9 +23,11 @@
 // 8 - d), each time with half the coefficients; a half step (one-warp teams,
 // every group diagonal) runs rounds 1-4 only, round 4 at half coefficients.
 // ctrl[step][group of the warp] packs A, B, a valid flag and the half-step
-// flag (set on all four groups of a half step); rec[step][round][lane] holds the pair
-// coefficients (c12, cn, qq, ds) -- cn = c6 for 12-6 pairs, -c10 for 12-10
-// H-bond pairs -- zero for pairs outside the pair list.
+// flag (set on all four groups of a half step).  Pair coefficients (c12, cn,
+// qq, ds) -- cn = c6 for 12-6 pairs, -c10 for 12-10 H-bond pairs -- zero for
+// pairs outside the pair list, by round pair: rounds (d, d + 1) = (2p, 2p + 1),
+// or (2p + 1, 2p + 2) in a half step; rec[step][p][0][lane] = (c12, c12', cn,
+// cn') and rec[step][p][1][lane] = (qq, qq', ds, ds'), ' = round d + 1.
 struct SchedDev {
     const uint32_t *ctrl;
     const float4 *rec;
@@ -83,7 +85,7 @@ struct GridDev {
 // Shared-memory scratch of one evaluating team, offsets in floats (each a
 // multiple of 4 so float4 views are aligned).
 struct EvalLayout {
-    int geno, grad, red, M, fs, x, f, tq, pf, cst, total;
+    int geno, grad, red, M, fs, x, z, f, tq, pf, cst, total;
 };
 
 __host__ __device__ inline int round4(int v) { return (v + 3) & ~3; }
@@ -97,7 +99,8 @@ __host__ __device__ inline EvalLayout eval_layout(int n_atoms, int n_frag, int n
     w.red = o; o += 32;               // team sums: two halves of 8 warp partials, then 8 energy partials
     w.M = o; o += 12 * n_frag * W;    // a copy per warp
     w.fs = o; o += grad ? 8 * n_frag : 0;
-    w.x = o; o += 4 * nb8 * W;        // a copy per warp
+    w.x = o; o += 4 * nb8;            // positions, pair-major: (x, x', y, y') per atom
+    w.z = o; o += 2 * nb8;            // (z, z') per atom
     w.f = o; o += grad ? 4 * nb8 : 0;
     w.tq = o; o += grad ? 4 * n_atoms : 0;
     w.pf = o; o += (grad && W > 1) ? 4 * 4 * W * (nb8 + 4) : 0;  // rows nb8 + 4 apart; W = 1 adds straight into f
