@@ -432,13 +432,14 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
         }
     }
     // Force accumulators start at zero: W = 1 adds pair forces straight into
-    // the per-atom forces, W > 1 into per-group partials.
+    // the per-atom forces, W > 1 into per-group partials (zeroed by warps
+    // 1.., while warp 0 composes the tree).
     float4 *Fv = reinterpret_cast<float4 *>(ws + Y.f);
     if (GRAD) {
         if (W == 1)
             for (int k = r; k < NB; k += S) Fv[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-        else
-            for (int k = r; k < 4 * W * PS; k += S) PF[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        else if (r >= 32)
+            for (int k = r - 32; k < 4 * W * PS; k += S - 32) PF[k] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     tm.sync();
 
