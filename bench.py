@@ -651,8 +651,8 @@ def pair_list(lig):
 # launch on the drug-size workload, from one ncu capture (cold caches), and a
 # digest of the kernel sources and input generator it was taken on: the figure
 # is reported only while they are unchanged.
-LS_TRAFFIC_BYTES = 31.06e6
-LS_TRAFFIC_SOURCES = "e9ab79a8480ed755"
+LS_TRAFFIC_BYTES = 31.04e6
+LS_TRAFFIC_SOURCES = "11428b18241892cb"
 
 
 # the files that define the local-search kernel and the ligand it runs on

@@ -571,7 +571,11 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
     // force (W = 1: the pair force in Fv plus the grid part; W > 1: the grid
     // part plus the partial rows of the groups whose steps touched the atom's
     // block, ascending group order) and the torque (x_i - t) x f_i.
-    float4 *Tq = reinterpret_cast<float4 *>(ws + Y.tq);
+    // W = 1 keeps the torques (and below the fragment sums) in the staged-cell
+    // area: atom i's torque goes to its own first cell slot, written by the
+    // thread that has just read that atom's cells
+    float4 *Tq = W == 1 ? Cst : reinterpret_cast<float4 *>(ws + Y.tq);
+    constexpr int TS = W == 1 ? 6 : 1;  // float4 stride of the torques
     const uint32_t *gmask = L.sched[W == 1 ? 0 : W == 2 ? 1 : W == 4 ? 2 : 3].gmask;
     for (int i = r; i < N; i += S) {
         const float3 xi = pos(i);
@@ -596,7 +600,7 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
                     }
             }
             Fv[i] = make_float4(fx, fy, fz, 0.f);
-            Tq[i] = make_float4(xi.y * fz - xi.z * fy, xi.z * fx - xi.x * fz, xi.x * fy - xi.y * fx, 0.f);
+            Tq[TS * i] = make_float4(xi.y * fz - xi.z * fy, xi.z * fx - xi.x * fz, xi.x * fy - xi.y * fx, 0.f);
         }
     }
     if (!GRAD) return team_sum(tm, e, red);
@@ -611,7 +615,9 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
     // fragments it moves (a contiguous run in depth-first order).  W > 1:
     // torsion k sums its contiguous atom range directly.  Range T is the
     // whole ligand (translation and rotation).  m lanes per range, butterfly.
-    float4 *FS = reinterpret_cast<float4 *>(ws + Y.fs);
+    // W = 1: fragment f's sums in slots 6f + 1 and 6f + 2 of the staged-cell
+    // area (dead once every atom's grid term is done; the torques hold slot 0)
+    float4 *FS = Cst + 1;
     const int F = L.n_frag;
     if (W == 1) {
         const int ml = lanes_log2(F, S, 32), m = 1 << ml, sub = r & (m - 1);
@@ -626,14 +632,14 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
             }
             float a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0, a5 = 0;
             for (int i = lo + sub; i < hi; i += m) {
-                const float4 fv = Fv[i], t = Tq[i];
+                const float4 fv = Fv[i], t = Tq[TS * i];
                 a0 += fv.x; a1 += fv.y; a2 += fv.z;
                 a3 += t.x; a4 += t.y; a5 += t.z;
             }
             group_sum6(a0, a1, a2, a3, a4, a5, ml);
             if (act && sub == 0) {
-                FS[2 * f] = make_float4(a0, a1, a2, 0.f);
-                FS[2 * f + 1] = make_float4(a3, a4, a5, 0.f);
+                FS[6 * f] = make_float4(a0, a1, a2, 0.f);
+                FS[6 * f + 1] = make_float4(a3, a4, a5, 0.f);
             }
         }
         tm.sync();
@@ -660,7 +666,7 @@ __device__ float eval_team(const LigandDev &L, const GridDev &G, float *ws, cons
             float a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0, a5 = 0;
 #pragma unroll 4
             for (int j = lo + sub; j < hi; j += m) {
-                const float4 u = W == 1 ? FS[2 * j] : Fv[j], v = W == 1 ? FS[2 * j + 1] : Tq[j];
+                const float4 u = W == 1 ? FS[6 * j] : Fv[j], v = W == 1 ? FS[6 * j + 1] : Tq[TS * j];
                 a0 += u.x; a1 += u.y; a2 += u.z;
                 a3 += v.x; a4 += v.y; a5 += v.z;
             }

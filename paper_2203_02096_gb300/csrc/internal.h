@@ -98,11 +98,11 @@ __host__ __device__ inline EvalLayout eval_layout(int n_atoms, int n_frag, int n
     w.grad = o; o += 48;
     w.red = o; o += 32;               // team sums: two halves of 8 warp partials, then 8 energy partials
     w.M = o; o += 12 * n_frag * W;    // a copy per warp
-    w.fs = o; o += grad ? 8 * n_frag : 0;
+    w.fs = o;                         // W = 1: fragment sums live in the staged-cell area (cst)
     w.x = o; o += 4 * nb8;            // positions, pair-major: (x, x', y, y') per atom
     w.z = o; o += 2 * nb8;            // (z, z') per atom
     w.f = o; o += grad ? 4 * nb8 : 0;
-    w.tq = o; o += grad ? 4 * n_atoms : 0;
+    w.tq = o; o += (grad && W > 1) ? 4 * n_atoms : 0;  // W = 1: torques live in cst
     w.pf = o; o += (grad && W > 1) ? 4 * 4 * W * (nb8 + 4) : 0;  // rows nb8 + 4 apart; W = 1 adds straight into f
     w.cst = o; o += 24 * nb8;  // staged map cells: 6 float4 per atom
     w.total = round4(o);
