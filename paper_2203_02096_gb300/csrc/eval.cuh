@@ -11,9 +11,10 @@
 // independent chains are too few to fill the GPU: the team splits atoms,
 // pairs and force gathers, like the paper's threads-per-block knob.
 //
-// GB300 layout: pose, forces and per-pair force scalars live in shared
-// memory; ligand constants come through L1 (read-only path); each atom-map
-// read is one 32-byte sector of the cell-major grid copy, L2-resident.
+// GB300 layout: pose, forces, torques and staged map cells live in shared
+// memory; ligand constants and pair records come through L1 (read-only
+// path); each atom-map read is one 32-byte cell (two adjacent quads) of the
+// z-column quad grid copy, L2-resident.
 // Every reduction has a fixed order (strided partial sums, xor butterflies,
 // then warps in index order), so results are bit-reproducible run to run.
 #pragma once

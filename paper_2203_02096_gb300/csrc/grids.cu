@@ -1,12 +1,13 @@
-// grids.cu -- receptor grid maps on the device: the cell-major copy read by
-// the evaluator, and the direct-sum map builder (the "reaction field for the
+// grids.cu -- receptor grid maps on the device: the z-column quad copy read
+// by the evaluator, and the direct-sum map builder (the "reaction field for the
 // protein" of Section II-A computed from receptor atoms).
 #include "forcefield.h"
 #include "internal.h"
 
 namespace {
 
-// Cell-major copy: thread per (cell, map), 8 corner values -> 2 float4.
+// Z-column quad copy: thread per (column, z plane, map), the quad of node
+// values (ix, iy), (ix+1, iy), (ix, iy+1), (ix+1, iy+1) -> one float4.
 __global__ void relayout_kernel(const float *__restrict__ nodes, int nx, int ny, int nz, int M, float4 *cells) {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long ncol = (long long)(nx - 1) * (ny - 1);
