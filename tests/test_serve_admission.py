@@ -1,0 +1,127 @@
+"""Host logic of the serving loop (serve.run) against a fake server, on the
+CPU: requests are admitted in arrival order while their device memory fits
+the budget and the server has free task slots; a refused request's ligand
+is released; every request completes with its own results; the memory in
+use never exceeds the budget while more than one request is in flight."""
+import numpy as np
+import pytest
+
+from paper_2203_02096_gb300 import capi, serve
+
+
+class FakeLigand:
+    live = 0
+
+    def __init__(self, lig):
+        self.n_genes = 7 + lig["torsions"]
+        self.bytes = lig["bytes"]
+        self.name = lig["name"]
+        FakeLigand.live += 1
+
+    def device_bytes(self):
+        return self.bytes
+
+    def free(self):
+        FakeLigand.live -= 1
+
+
+class FakeServer:
+    """Task slots with a fixed capacity; a request's runs finish after a
+    fixed number of polls."""
+
+    def __init__(self, capacity, polls_to_finish=3):
+        self.capacity, self.polls = capacity, polls_to_finish
+        self.next_task = 0
+        self.active = {}            # first task -> [nruns, polls left, ligand name]
+        self.order = []             # ligand names in submit order
+        self.in_use = 0
+
+    def submit(self, grids, lig, params, seed):
+        if self.in_use + params.nruns > self.capacity:
+            return None
+        first = self.next_task
+        self.next_task += params.nruns
+        self.in_use += params.nruns
+        self.active[first] = [params.nruns, self.polls, lig.name]
+        self.order.append(lig.name)
+        return first
+
+    def done(self, first, nruns):
+        rec = self.active[first]
+        rec[1] -= 1
+        return rec[1] <= 0
+
+    def result(self, first, nruns, n_genes):
+        rec = self.active.pop(first)
+        self.in_use -= rec[0]
+        g = np.full((nruns, n_genes), float(first), np.float32)
+        return g, np.full(nruns, -float(first)), np.full(nruns, 100, np.int64)
+
+
+@pytest.fixture
+def fake_capi(monkeypatch):
+    FakeLigand.live = 0
+    monkeypatch.setattr(capi, "ligand_from", lambda ctx, lig: FakeLigand(lig))
+    yield
+
+
+def _requests(n, seed=0):
+    rng = np.random.default_rng(seed)
+    arrivals = np.sort(rng.uniform(0.0, 0.02, size=n))
+    return [serve.Request({"name": k, "torsions": int(rng.integers(0, 8)), "bytes": int(rng.integers(1, 5)) << 20},
+                          0, seed=k, arrival=float(a)) for k, a in enumerate(arrivals)]
+
+
+def test_all_requests_complete_in_arrival_order(fake_capi):
+    reqs = _requests(24)
+    params = capi.default_params(nruns=4)
+    srv = FakeServer(capacity=16)
+    rep = serve.run(None, srv, [None], reqs, params, mem_budget=64 << 20, poll_sleep=1e-4, timeout=30.0)
+    assert len(rep.done) == len(reqs)
+    assert srv.order == [r.ligand["name"] for r in sorted(reqs, key=lambda r: r.arrival)]
+    assert FakeLigand.live == 0                      # every ligand handle released
+    assert 1 <= rep.max_in_flight <= 4               # 16 slots / 4 runs per request
+    for d in rep.done:
+        assert d.latency >= 0.0
+        assert d.best_geno.shape == (4, d.request.ligand["torsions"] + 7)
+        assert np.all(d.evals == 100)
+    s = rep.summary()
+    assert s["requests"] == len(reqs) and s["p99_s"] >= s["p50_s"] >= 0.0
+
+
+def test_memory_budget_bounds_the_requests_in_flight(fake_capi, monkeypatch):
+    reqs = _requests(20, seed=1)
+    params = capi.default_params(nruns=2)
+    budget = 9 << 20
+    srv = FakeServer(capacity=1 << 10, polls_to_finish=5)
+    peak = {"bytes": 0, "in_flight": 0}
+    submit = srv.submit
+
+    def watched_submit(grids, lig, p, seed):
+        first = submit(grids, lig, p, seed)
+        if first is not None:
+            live = sum(r.ligand["bytes"] + p.nruns * serve.ROW_BYTES for r in reqs
+                       if r.ligand["name"] in [v[2] for v in srv.active.values()])
+            if len(srv.active) > 1:
+                assert live <= budget, (live, budget)
+            peak["bytes"] = max(peak["bytes"], live)
+            peak["in_flight"] = max(peak["in_flight"], len(srv.active))
+        return first
+
+    monkeypatch.setattr(srv, "submit", watched_submit)
+    rep = serve.run(None, srv, [None], reqs, params, mem_budget=budget, poll_sleep=1e-4, timeout=30.0)
+    assert len(rep.done) == len(reqs)
+    assert peak["in_flight"] >= 2                    # the budget admits several 1-4 MB requests at once
+    assert FakeLigand.live == 0
+
+
+def test_a_request_larger_than_the_budget_runs_alone(fake_capi):
+    reqs = [serve.Request({"name": 0, "torsions": 2, "bytes": 1 << 20}, 0, seed=0, arrival=0.0),
+            serve.Request({"name": 1, "torsions": 2, "bytes": 64 << 20}, 0, seed=1, arrival=0.0),
+            serve.Request({"name": 2, "torsions": 2, "bytes": 1 << 20}, 0, seed=2, arrival=0.0)]
+    params = capi.default_params(nruns=1)
+    srv = FakeServer(capacity=64)
+    rep = serve.run(None, srv, [None], reqs, params, mem_budget=8 << 20, poll_sleep=1e-4, timeout=30.0)
+    assert [d.request.ligand["name"] for d in rep.done] == [0, 1, 2]
+    assert srv.order == [0, 1, 2]
+    assert FakeLigand.live == 0
