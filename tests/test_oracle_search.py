@@ -88,6 +88,73 @@ def test_ga_children_structure_and_rates(small_system, oracle_mod):
     assert abs(mut / nblk - 0.02) < 0.005
 
 
+def _ks_uniform(x, lo, hi):
+    """Kolmogorov-Smirnov distance of a sample from U(lo, hi)."""
+    x = np.sort(np.asarray(x, np.float64))
+    n = len(x)
+    F = np.clip((x - lo) / (hi - lo), 0.0, 1.0)
+    i = np.arange(1, n + 1)
+    return max(np.max(i / n - F), np.max(F - (i - 1) / n))
+
+
+def _qmul(a, b):
+    """Hamilton product of quaternions (w, x, y, z), rows of a and b."""
+    aw, ax, ay, az = a.T
+    bw, bx, by, bz = b.T
+    return np.stack([aw * bw - ax * bx - ay * by - az * bz,
+                     aw * bx + ax * bw + ay * bz - az * by,
+                     aw * by - ax * bz + ay * bw + az * bx,
+                     aw * bz + ax * by - ay * bx + az * bw], axis=1)
+
+
+def test_ga_mutation_sizes(small_system, oracle_mod):
+    """The sizes of the mutations (the reading of the GA's mutation operator):
+    translation += U(-2, 2) A, torsion += U(-pi, pi) then wrapped,
+    orientation <- normalise((1, v) (x) q) with v uniform in [-1, 1)^3.
+    With crossover off and every block mutated, each child block is its first
+    parent's block plus one mutation, so the deltas are recovered exactly
+    (up to the FP32 rounding of the update) and compared, by Kolmogorov-
+    Smirnov distance, with the distribution the reading states.  A range or
+    scale slip (U(-1, 1), U(0, 2), a 10% stretch), a torsion delta drawn on
+    [0, 2 pi) or the product taken as q (x) (1, v) moves a distance far beyond
+    the 1e-3 significance level used (1.95 / sqrt(n))."""
+    L, grid = small_system["olig"], small_system["grid"]
+    nt, popn = L.n_torsions, 150
+    params = oracle_mod.make_params(pop_size=popn, p_cross=0.0, p_mut=1.0)
+    dt, dtau, v, ang = [], [], [], []
+    for gen in range(1, 31):
+        pop = oracle_mod.init_population(nt, grid, seed=100 + gen, run=0, pop=popn)
+        E = np.arange(popn, dtype=np.float64)
+        kids, info, _ = oracle_mod.ga_children(nt, pop, E, seed=5, run=1, gen=gen, params=params)
+        p1 = info[1:, 0].astype(int)
+        assert np.all(info[1:, 2] == info[1:, 3])                       # no crossover
+        assert np.all(info[1:, 4] == (1 << (4 + nt)) - 1)              # every block mutated
+        par, kid = pop[p1].astype(np.float64), kids[1:].astype(np.float64)
+        dt.append((kid[:, 0:3] - par[:, 0:3]).ravel())
+        dtau.append((((kid[:, 7:] - par[:, 7:]) + np.pi) % (2 * np.pi) - np.pi).ravel())
+        conj = par[:, 3:7] * np.array([1.0, -1.0, -1.0, -1.0])
+        r = _qmul(kid[:, 3:7], conj)                                    # = (1, v) / |(1, v)|
+        assert np.all(r[:, 0] > 0)
+        v.append(r[:, 1:4] / r[:, 0:1])
+        ang.append(2.0 * np.arccos(np.clip(r[:, 0], -1.0, 1.0)))
+    dt, dtau, v, ang = (np.concatenate(a) for a in (dt, dtau, v, ang))
+    crit = lambda n: 1.95 / np.sqrt(n)                                  # noqa: E731
+    assert _ks_uniform(dt, -2.0, 2.0) < crit(len(dt)), _ks_uniform(dt, -2.0, 2.0)
+    assert dt.min() < -1.99 and dt.max() > 1.99 and np.abs(dt).max() <= 2.0 + 1e-5
+    assert _ks_uniform(dtau, -np.pi, np.pi) < crit(len(dtau)), _ks_uniform(dtau, -np.pi, np.pi)
+    assert np.abs(v).max() <= 1.0 + 1e-5 and np.abs(v).max() > 0.99
+    for c in range(3):
+        assert _ks_uniform(v[:, c], -1.0, 1.0) < crit(len(v)), (c, _ks_uniform(v[:, c], -1.0, 1.0))
+    assert abs(np.corrcoef(v.T)[0, 1]) < 0.05 and abs(np.corrcoef(v.T)[1, 2]) < 0.05
+    # the rotation angle 2 atan|v| against the angle of v drawn by numpy
+    ref = np.random.default_rng(0).uniform(-1.0, 1.0, size=(400_000, 3))
+    ref_ang = np.sort(2.0 * np.arctan(np.linalg.norm(ref, axis=1)))
+    a = np.sort(ang)
+    Fa = np.arange(1, len(a) + 1) / len(a)
+    Fr = np.searchsorted(ref_ang, a, side="right") / len(ref_ang)
+    assert np.max(np.abs(Fa - Fr)) < crit(len(a)), np.max(np.abs(Fa - Fr))
+
+
 def test_ls_picks(oracle_mod):
     counts = np.zeros(150)
     for gen in range(2000):
