@@ -322,9 +322,14 @@ int server_destroy(dock_server *srv);
  *  - A request needing more scratch than the array holds (about
  *    2 * nruns * pop_size * (4*G + 4) bytes) fails with DOCK_ERR_SIZE and a
  *    message giving the bytes needed.
- *  - The first call on a device looks up the array's device address
- *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture.  The context's device must be current.
+ *  - dock_create looks up the array's device address (cudaGetSymbolAddress)
+ *    with its device current.  That lookup loads the library's device code,
+ *    which the CUDA runtime otherwise loads on first use, so the array is
+ *    allocated when the context is created, not by a later call.  If that
+ *    lookup failed, the first dock_async_noalloc call on the device repeats
+ *    it; so create the context before any stream capture and before the
+ *    application pools the rest of the device memory.  The context's device
+ *    must be current when calling.
  *  - All calls share the one array and it keeps the last call's contents
  *    (the counters are cleared at the start of each call): calls that
  *    overlap on the GPU -- on different streams, or from different host
@@ -349,6 +354,22 @@ int dock_async_noalloc(dock_ctx *ctx, const dock_grids *grids, const dock_ligand
  * dock_local_search: ADADELTA from B start points x0 [B][G], iters
  * iterations each, `threads` per chain as in dock_params.ls_threads;
  * x_best [B][G] (unit quaternion) and E_best [B].
+ * dock_local_search_trace: the same search, also recording every iteration
+ * it of chain b: the point evaluated (x_trace [B][iters][G], quaternion as
+ * stored, unnormalised), its gradient (g_trace [B][iters][G]) and energy
+ * (E_trace [B][iters]).  The three trace pointers are given together or all
+ * NULL (then it is dock_local_search).  Caller-owned device buffers.
+ * dock_adadelta_step: one ADADELTA update (Zeiler 2012; the local search of
+ * the memetic step, paper Section II-A) of B points [B][n_genes] in place,
+ * given their gradients g [B][n_genes] and running averages Eg2, Edx2
+ * [B][n_genes] (updated in place): per gene
+ *     Eg2 <- rho Eg2 + (1 - rho) g^2
+ *     dx  <- -sqrt(Edx2 + eps) / sqrt(Eg2 + eps) * g
+ *     Edx2 <- rho Edx2 + (1 - rho) dx^2,   x <- x + dx,
+ * then torsion genes (index >= 7) wrapped to [-pi, pi).  It is the update
+ * dock_local_search applies after each evaluation, exposed on its own so it
+ * can be checked gene by gene.  Errors: n_genes outside 7..39, rho outside
+ * [0, 1), eps <= 0, B * n_genes > INT_MAX.
  * dock_philox: out[n][4] = Philox4x32-10(ctr[n][4], key = (key_lo, key_hi)). */
 int dock_init_population(dock_ctx *ctx, const dock_grids *grids, int n_torsions, int pop, int nruns,
                          uint64_t seed, float *pop_out, void *stream);
@@ -359,6 +380,11 @@ int dock_ls_picks(dock_ctx *ctx, int pop, int n_ls, int nruns, uint64_t seed, ui
                   void *stream);
 int dock_local_search(dock_ctx *ctx, const dock_grids *grids, const dock_ligand *lig, const float *x0, int B,
                       int iters, float rho, float eps, int threads, float *x_best, float *E_best, void *stream);
+int dock_local_search_trace(dock_ctx *ctx, const dock_grids *grids, const dock_ligand *lig, const float *x0, int B,
+                            int iters, float rho, float eps, int threads, float *x_best, float *E_best,
+                            float *x_trace, float *g_trace, float *E_trace, void *stream);
+int dock_adadelta_step(dock_ctx *ctx, int B, int n_genes, float rho, float eps, float *x, const float *g,
+                       float *Eg2, float *Edx2, void *stream);
 int dock_philox(dock_ctx *ctx, const uint32_t *ctr, int n, uint32_t key_lo, uint32_t key_hi, uint32_t *out,
                 void *stream);
 /* dock_solis_wets: the Solis-Wets local search (paper, Section II-A; Solis

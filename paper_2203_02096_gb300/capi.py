@@ -79,6 +79,8 @@ SIGNATURES = {
     "dock_ga_children": (_i, [_vp, _i, _i, _i, _vp, _vp, _u64, _u32, _P(DockParams), _vp, _vp, _vp]),
     "dock_ls_picks": (_i, [_vp, _i, _i, _i, _u64, _u32, _vp, _vp]),
     "dock_local_search": (_i, [_vp, _vp, _vp, _vp, _i, _i, _f, _f, _i, _vp, _vp, _vp]),
+    "dock_local_search_trace": (_i, [_vp, _vp, _vp, _vp, _i, _i, _f, _f, _i, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "dock_adadelta_step": (_i, [_vp, _i, _i, _f, _f, _vp, _vp, _vp, _vp, _vp]),
     "dock_philox": (_i, [_vp, _vp, _i, _u32, _u32, _vp, _vp]),
     "dock_tune": (_i, [_vp, _vp, _vp, _i, _P(DockParams), _i, _vp, _i, _i, _vp]),
     "dock_set_option": (_i, [_vp, _i, _i]),
@@ -454,6 +456,35 @@ def dock_local_search(ctx, grids, lig, x0: torch.Tensor, iters: int, rho=0.8, ep
     ctx.check(ctx.lib.dock_local_search(ctx.h, grids.h, lig.h, _ptr(x0), B, int(iters), float(rho), float(eps),
                                         int(threads), _ptr(xb), _ptr(Eb), _stream(stream)), "dock_local_search")
     return xb, Eb
+
+
+def dock_local_search_trace(ctx, grids, lig, x0: torch.Tensor, iters: int, rho=0.8, eps=1e-2, threads=0,
+                            stream=None):
+    """ADADELTA as dock_local_search, plus every iteration's point, gradient
+    and energy: returns (x_best, E_best, x_trace [B, iters, G], g_trace
+    [B, iters, G], E_trace [B, iters]), device tensors."""
+    B, G = x0.shape
+    xb = torch.empty_like(x0)
+    Eb = torch.empty(B, dtype=torch.float32, device=x0.device)
+    xt = torch.empty((B, iters, G), dtype=torch.float32, device=x0.device)
+    gt = torch.empty((B, iters, G), dtype=torch.float32, device=x0.device)
+    Et = torch.empty((B, iters), dtype=torch.float32, device=x0.device)
+    ctx.check(ctx.lib.dock_local_search_trace(ctx.h, grids.h, lig.h, _ptr(x0), B, int(iters), float(rho), float(eps),
+                                              int(threads), _ptr(xb), _ptr(Eb), _ptr(xt), _ptr(gt), _ptr(Et),
+                                              _stream(stream)), "dock_local_search_trace")
+    return xb, Eb, xt, gt, Et
+
+
+def dock_adadelta_step(ctx, x: torch.Tensor, g: torch.Tensor, Eg2: torch.Tensor, Edx2: torch.Tensor, rho=0.8,
+                       eps=1e-2, stream=None):
+    """One ADADELTA update of the rows of x in place (Eg2, Edx2 updated in
+    place too); all four [B, G] FP32 device tensors."""
+    B, G = x.shape
+    for t in (g, Eg2, Edx2):
+        if t.shape != x.shape or t.dtype != torch.float32 or not t.is_contiguous():
+            raise ValueError("g, Eg2, Edx2 must be contiguous FP32 tensors shaped like x")
+    ctx.check(ctx.lib.dock_adadelta_step(ctx.h, B, G, float(rho), float(eps), _ptr(x), _ptr(g), _ptr(Eg2), _ptr(Edx2),
+                                         _stream(stream)), "dock_adadelta_step")
 
 
 def dock_solis_wets(ctx, grids, lig, x0: torch.Tensor, params: DockParams, E0: torch.Tensor | None = None,

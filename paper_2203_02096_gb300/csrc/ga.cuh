@@ -243,13 +243,21 @@ __device__ __forceinline__ float wrap_any(float x) {
     return x - kTwoPiF * floorf((x + kPiF) * (1.f / kTwoPiF));
 }
 
+// Optional per-iteration record of one ADADELTA chain: the point evaluated
+// at iteration it (x[it][G]), its gradient (g[it][G]) and energy (E[it]).
+// Null pointers record nothing.
+struct LsTrace {
+    float *x, *g, *E;
+};
+
 // ADADELTA from xi for iters iterations by a team of W warps (warp 0 owns
 // the genes: lane l holds genes l and l + 32); the best point seen, its
 // quaternion normalised, is written to xo (which may alias xi).  Returns the
-// best energy (on warp 0).
+// best energy (on warp 0).  tr (optional) records every iteration.
 template <int W>
 __device__ float ls_chain(const LigandDev &L, const GridDev &G, float *ws, const EvalLayout &Y,
-                          const dev::Team<W> &tm, const float *xi, float *xo, int iters, float rho, float eps) {
+                          const dev::Team<W> &tm, const float *xi, float *xo, int iters, float rho, float eps,
+                          LsTrace tr = LsTrace{nullptr, nullptr, nullptr}) {
     const int Gn = L.n_genes;
     // warp 0 owns the genes: lane l holds genes l and l + 32
     const bool w0 = tm.warp() == 0;
@@ -269,6 +277,12 @@ __device__ float ls_chain(const LigandDev &L, const GridDev &G, float *ws, const
         // the evaluator's warp 0 reads the genes after a __syncwarp; the
         // other warps read them only after the team's barriers
         const float e = dev::eval_team<W, true>(L, G, ws, Y, tm);
+        if (w0 && tr.x) {
+            float *tx = tr.x + (size_t)it * Gn, *tg = tr.g + (size_t)it * Gn;
+            if (j0 < Gn) { tx[j0] = x0; tg[j0] = ws[Y.grad + j0]; }
+            if (j1 < Gn) { tx[j1] = x1; tg[j1] = ws[Y.grad + j1]; }
+            if (lane == 0) tr.E[it] = e;
+        }
         if (w0) {
             if (e < best) {
                 best = e;

@@ -9,6 +9,7 @@
 // operation per step (__fadd_rn & co., never contracted), so that given the
 // same energies and the same Philox stream they are reproducible exactly by
 // any IEEE single-precision implementation.
+#include <limits.h>
 #include <math.h>
 
 #include <cmath>
@@ -105,12 +106,14 @@ __global__ void picks_kernel(int pop, int n_ls, int nruns, uint2 key, uint32_t g
 // one-warp teams per block; W > 1: the block is the team).  With picks
 // (inside dock): chain c is pick c % n_ls of run c / n_ls, updated in place
 // in the population; without: chain c starts at x_in[c] and writes x_out[c].
+// trace (x, g, E null inside dock): chain c records its iterations at
+// x + c iters G, g + c iters G, E + c iters.
 // Residency: W = 8 keeps 3 blocks (24 warps) per SM, W = 4 four, W = 2 eight.
 template <int W>
 __global__ void __launch_bounds__(W == 1 ? 128 : 32 * W, W == 8 ? 3 : W == 4 ? 4 : W == 2 ? 8 : 4)
 ls_kernel(LigandDev L, GridDev G, float *x_in, float *E_pop, const int *__restrict__ picks, int pop, int n_ls,
           int nchains, int iters, float rho, float eps, float *x_out, float *E_out, unsigned long long *evals,
-          EvalLayout Y) {
+          EvalLayout Y, LsTrace trace) {
     extern __shared__ float4 smem4[];
     const int team_in_block = W == 1 ? (threadIdx.x >> 5) : 0;
     float *ws = reinterpret_cast<float *>(smem4) + team_in_block * Y.total;
@@ -131,7 +134,12 @@ ls_kernel(LigandDev L, GridDev G, float *x_in, float *E_pop, const int *__restri
         xo = x_out + (size_t)c * Gn;
         eo = E_out + c;
     }
-    const float best = ls_chain<W>(L, G, ws, Y, tm, xi, xo, iters, rho, eps);
+    LsTrace tr{nullptr, nullptr, nullptr};
+    if (trace.x) {
+        const size_t o = (size_t)c * iters;
+        tr = LsTrace{trace.x + o * Gn, trace.g + o * Gn, trace.E + o};
+    }
+    const float best = ls_chain<W>(L, G, ws, Y, tm, xi, xo, iters, rho, eps, tr);
     if (tm.rank == 0) {
         *eo = best;
         if (evals) atomicAdd(evals + run, (unsigned long long)iters);
@@ -238,6 +246,20 @@ __global__ void evals_out_kernel(const unsigned long long *ev, int n, int64_t *o
     if (i < n) out[i] = (int64_t)ev[i];
 }
 
+// One ADADELTA update of every gene of B points (the step ls_chain takes
+// after each evaluation), torsion genes (index >= 7) wrapped to [-pi, pi).
+__global__ void adadelta_step_kernel(int n, int Gn, float rho, float eps, float *x, const float *__restrict__ g,
+                                     float *eg2, float *edx2) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float xi = x[i], a = eg2[i], b = edx2[i];
+    adadelta(xi, g[i], a, b, rho, eps);
+    if (i % Gn >= 7) xi = wrap_any(xi);
+    x[i] = xi;
+    eg2[i] = a;
+    edx2[i] = b;
+}
+
 __global__ void philox_kernel(const uint32_t *ctr, int n, uint2 key, uint32_t *out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -291,6 +313,9 @@ int resolve_params(dock_ctx *ctx, const dock_params *in, dock_params &p) {
     if (p.pop_size < 2 || p.pop_size > (1 << 20) || p.nruns < 1 || p.max_evals < 0 || p.ls_count > p.pop_size ||
         p.ls_count > kMaxLs || p.ls_iters < 0 || !(p.rho >= 0.f && p.rho < 1.f) || !(p.eps > 0.f))
         return set_err(ctx, DOCK_ERR_INVALID, "invalid dock_params");
+    // kernels index individuals (run, slot) with an int
+    if ((long long)p.nruns * p.pop_size > INT_MAX)
+        return set_err(ctx, DOCK_ERR_INVALID, "nruns * pop_size exceeds INT_MAX");
     return check_sw(ctx, p);
 }
 
@@ -427,7 +452,9 @@ int dock_async(dock_ctx *ctx, const dock_grids *grids, const dock_ligand *lig, c
                     int iters = P.ls_iters;
                     float rho = P.rho, eps = P.eps;
                     int nl = nls, ch = chains, popn = pop;
-                    void *c[] = {&l, &g, &popB, &EB, &picks, &popn, &nl, &ch, &iters, &rho, &eps, &no_out, &no_out, &ev, &wg};
+                    LsTrace no_trace{nullptr, nullptr, nullptr};
+                    void *c[] = {&l,   &g,   &popB,   &EB,     &picks, &popn, &nl,      &ch,
+                                 &iters, &rho, &eps, &no_out, &no_out, &ev,   &wg,  &no_trace};
                     if (!e) e = launch_ls(ctx, lw, chains, Wg, s, "dock_ls", c);
                 }
                 std::swap(popA, popB);
@@ -601,11 +628,14 @@ int dock_ls_picks(dock_ctx *ctx, int pop, int n_ls, int nruns, uint64_t seed, ui
     return e ? cuda_err(ctx, e, "picks kernel") : DOCK_OK;
 }
 
-int dock_local_search(dock_ctx *ctx, const dock_grids *grids, const dock_ligand *lig, const float *x0, int B,
-                      int iters, float rho, float eps, int threads, float *x_best, float *E_best, void *stream) {
+int dock_local_search_trace(dock_ctx *ctx, const dock_grids *grids, const dock_ligand *lig, const float *x0, int B,
+                            int iters, float rho, float eps, int threads, float *x_best, float *E_best,
+                            float *x_trace, float *g_trace, float *E_trace, void *stream) {
     if (!ctx || !grids || !lig || (B > 0 && (!x0 || !x_best || !E_best)) || B < 0 || iters < 1 ||
         !(rho >= 0.f && rho < 1.f) || !(eps > 0.f))
         return ctx ? set_err(ctx, DOCK_ERR_INVALID, "invalid argument") : DOCK_ERR_INVALID;
+    if ((x_trace || g_trace || E_trace) && !(x_trace && g_trace && E_trace))
+        return set_err(ctx, DOCK_ERR_INVALID, "x_trace, g_trace and E_trace go together");
     int rc = check_maps(ctx, grids, lig);
     if (rc) return rc;
     if (B == 0) return DOCK_OK;
@@ -622,9 +652,32 @@ int dock_local_search(dock_ctx *ctx, const dock_grids *grids, const dock_ligand 
     const int *no_picks = nullptr;
     unsigned long long *no_ev = nullptr;
     int zero = 0, one = 1;
-    void *a[] = {&l, &g, &xin, &no_pop, &no_picks, &zero, &one, &B, &iters, &rho, &eps, &x_best, &E_best, &no_ev, &W};
+    LsTrace tr{x_trace, g_trace, E_trace};
+    void *a[] = {&l,   &g,   &xin,    &no_pop, &no_picks, &zero, &one, &B,
+                 &iters, &rho, &eps, &x_best, &E_best,   &no_ev, &W,   &tr};
     cudaError_t e = launch_ls(ctx, lw, B, W, (cudaStream_t)stream, "local_search", a);
     return e ? cuda_err(ctx, e, "local search kernel") : DOCK_OK;
+}
+
+int dock_local_search(dock_ctx *ctx, const dock_grids *grids, const dock_ligand *lig, const float *x0, int B,
+                      int iters, float rho, float eps, int threads, float *x_best, float *E_best, void *stream) {
+    return dock_local_search_trace(ctx, grids, lig, x0, B, iters, rho, eps, threads, x_best, E_best, nullptr,
+                                   nullptr, nullptr, stream);
+}
+
+int dock_adadelta_step(dock_ctx *ctx, int B, int n_genes, float rho, float eps, float *x, const float *g,
+                       float *Eg2, float *Edx2, void *stream) {
+    if (!ctx || B < 0 || n_genes < 7 || n_genes > 7 + DOCK_MAX_TORSIONS || !(rho >= 0.f && rho < 1.f) || !(eps > 0.f) ||
+        (B > 0 && (!x || !g || !Eg2 || !Edx2)))
+        return ctx ? set_err(ctx, DOCK_ERR_INVALID, "invalid argument") : DOCK_ERR_INVALID;
+    const long long n = (long long)B * n_genes;
+    if (n == 0) return DOCK_OK;
+    if (n > INT_MAX) return set_err(ctx, DOCK_ERR_INVALID, "B * n_genes exceeds INT_MAX");
+    adadelta_step_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>((int)n, n_genes, rho, eps, x,
+                                                                                       g, Eg2, Edx2);
+    ++ctx->launches;
+    cudaError_t e = cudaGetLastError();
+    return e ? cuda_err(ctx, e, "ADADELTA step kernel") : DOCK_OK;
 }
 
 int dock_solis_wets(dock_ctx *ctx, const dock_grids *grids, const dock_ligand *lig, const float *x0,
@@ -728,7 +781,9 @@ int tune_ls_launch(dock_ctx *ctx, const dock_grids *grids, const dock_ligand *li
         uint2 key = make_uint2(1u, 2u);
         uint32_t run0 = 0, gen0 = 0;
         const float *e0p = E0;
-        void *la[] = {&l, &g, &x, &no_pop, &no_picks, &zero, &one, &chains, &iters, &rho, &eps, &xo, &Eo, &no_ev, &Y};
+        LsTrace no_trace{nullptr, nullptr, nullptr};
+        void *la[] = {&l,  &g,  &x,     &no_pop, &no_picks, &zero, &one, &chains, &iters,
+                      &rho, &eps, &xo, &Eo,    &no_ev,    &Y,    &no_trace};
         void *sa[] = {&l, &g, &x, &no_pop, &no_picks, &zero, &one, &chains, &iters, &S, &key, &run0, &gen0, &e0p,
                       &xo, &Eo, &no_ev, &no_eo, &no_active, &Y};
         auto one_launch = [&]() {
@@ -891,6 +946,14 @@ size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 }  // namespace
 
+// Called by dock_create with the context's device current: the lookup loads
+// this file's device code (modules load lazily), so the array exists from the
+// context's creation on and a later dock_async_noalloc allocates nothing.
+int noalloc_prepare(dock_ctx *ctx) {
+    unsigned char *base = nullptr;
+    return noalloc_base(ctx, &base);
+}
+
 extern "C" int dock_async_noalloc(dock_ctx *ctx, const dock_grids *grids, const dock_ligand *lig,
                                   const dock_params *params, uint64_t seed, float *best_geno, float *best_E32,
                                   double *best_E, int64_t *evals_used, void *stream) {
@@ -956,7 +1019,9 @@ extern "C" int dock_async_noalloc(dock_ctx *ctx, const dock_grids *grids, const 
             int iters = P.ls_iters;
             float rho = P.rho, eps = P.eps;
             int nl = nls, ch = chains, popn = pop;
-            void *c[] = {&l, &g, &popB, &EB, &picks, &popn, &nl, &ch, &iters, &rho, &eps, &no_out, &no_out, &ev, &wg};
+            LsTrace no_trace{nullptr, nullptr, nullptr};
+            void *c[] = {&l,   &g,   &popB,   &EB,     &picks, &popn, &nl,      &ch,
+                         &iters, &rho, &eps, &no_out, &no_out, &ev,   &wg,  &no_trace};
             if (!e) e = launch_ls(ctx, lw, chains, Wg, s, "dock_ls", c);
         }
         std::swap(popA, popB);
