@@ -167,6 +167,9 @@ int dock_create(dock_ctx **out, int device, const dock_allocator *alloc) {
         c->alloc = *alloc;
         c->has_alloc = true;
     }
+    // the no-allocation docking's array comes into being here, not in its
+    // first call; a failure is left for that call to report
+    if (noalloc_prepare(c) != DOCK_OK) cudaGetLastError();
     *out = c;
     return DOCK_OK;
 }

@@ -176,4 +176,6 @@ cudaError_t launch_rescore64(dock_ctx *ctx, const LigandDev &L, const GridDev &G
 cudaError_t launch_score(dock_ctx *ctx, const LigandDev &L, const GridDev &G, const float *geno, int B, float *E,
                          float *grad, cudaStream_t s);
 cudaError_t launch_pose(dock_ctx *ctx, const LigandDev &L, const float *geno, int B, float *xyz, cudaStream_t s);
+// Looks up the no-allocation scratch array on the current device (search.cu).
+int noalloc_prepare(dock_ctx *ctx);
 
