@@ -117,17 +117,19 @@ def _ks(a, b):
 
 
 def test_dock_small_ligand_workload(gpu, oracle_mod):
-    """The small-ligand workload in full (16 atoms, 40^3 x 7 maps, 10 runs x
-    100k evaluations): exact evaluation accounting, FP64 re-score equal to the
-    oracle's energy of the returned pose, deterministic, and best-energy
-    distribution matching the oracle's docking of the same inputs."""
+    """The small-ligand workload (16 atoms, 40^3 x 7 maps, 100k evaluations
+    per run) at 50 runs instead of 10: exact evaluation accounting, FP64
+    re-score equal to the oracle's energy of the returned pose,
+    deterministic, and best-energy distribution matching the oracle's docking
+    of the same inputs: medians within 0.5 kcal/mol and a two-sample KS
+    distance at most 0.3 (about the 2% level for 50 against 50 runs)."""
     w = synth.small_ligand_workload()
     maps = oracle_mod.build_maps(w.receptor, w.box).astype(np.float32)
     ogrid = oracle_mod.OracleGrid(maps, w.box)
     olig = oracle_mod.OracleLigand(w.ligand)
     L = capi.ligand_from(gpu, w.ligand)
     G = capi.grids_from_maps(gpu, maps, w.box)
-    P = _params(pop_size=w.pop_size, nruns=w.nruns, max_evals=w.max_evals, ls_iters=w.ls_iters)
+    P = _params(pop_size=w.pop_size, nruns=50, max_evals=w.max_evals, ls_iters=w.ls_iters)
     bg, bE, ev = capi.dock(gpu, G, L, P, w.seed)
     bg2, bE2, ev2 = capi.dock(gpu, G, L, P, w.seed)
     assert np.array_equal(bg, bg2) and np.array_equal(bE, bE2) and np.array_equal(ev, ev2)
@@ -138,5 +140,7 @@ def test_dock_small_ligand_workload(gpu, oracle_mod):
     assert np.allclose(bE, rescored, rtol=1e-9, atol=1e-9)
     assert np.allclose(np.linalg.norm(bg[:, 3:7], axis=1), 1.0, atol=1e-6)
     # distributions of the best energies over runs
+    print(f"\nsmall-ligand docking, 50 runs: median best E {np.median(bE):.3f} (oracle {np.median(oE):.3f}); "
+          f"KS {_ks(bE, oE):.2f}")
     assert abs(np.median(bE) - np.median(oE)) < 0.5, (np.sort(bE), np.sort(oE))
-    assert _ks(bE, oE) <= 0.7
+    assert _ks(bE, oE) <= 0.3, (np.sort(bE), np.sort(oE))
