@@ -15,8 +15,9 @@
  * random sample of each generation (Lamarckian write-back) minimises it over
  * several independent runs of population 150; the answer is the best pose
  * over all runs.  The paper prints none of the functional forms or constants:
- * every form and constant below is a reading fixed by this project and listed
- * as such in the design notes.  The local search is ADADELTA (Zeiler 2012),
+ * every form below is a reading (the AutoDock4 family's 12-6 / 12-10 pair
+ * potentials, Mehler-Solmajer dielectric, Gaussian desolvation) and every
+ * constant is defined by this project.  The local search is ADADELTA (Zeiler 2012),
  * which the paper reaches only through its citation of gradient-based local
  * search in AutoDock-GPU; the paper's own miniapp uses Solis-Wets, which
  * orc_solis_wets restates (Solis and Wets 1981, adaptive step with a bias
