@@ -103,6 +103,13 @@ typedef struct {
     int batch_warps;   /* warps per block of dock_batch's persistent kernel: 1, 2,
                           4, or 0 = as many (<= 4) as shared memory allows;
                           results do not depend on it; default 0                */
+    int batch_pack;    /* dock_batch packing: 0 = one launch over all tasks,
+                          largest ligands first (default); 1 = by atom count:
+                          ligands in classes of up to 32, 64, 96, 128 and 255
+                          atoms, one launch per class (largest class first),
+                          each sizing its shared memory, hence its warps per
+                          SM, for its own largest ligand; results do not
+                          depend on it                                          */
 } dock_params;
 
 /* Library version (major*10000 + minor*100 + patch). */

@@ -37,7 +37,8 @@ class DockParams(C.Structure):
     _fields_ = [("pop_size", _i), ("nruns", _i), ("max_evals", _i64), ("ls_count", _i), ("ls_iters", _i),
                 ("rho", _f), ("eps", _f), ("p_tour", _f), ("p_cross", _f), ("p_mut", _f), ("trans_mut", _f),
                 ("ls_threads", _i), ("ls_method", _i), ("sw_rho0", _f), ("sw_rho_lo", _f), ("sw_expand", _f),
-                ("sw_contract", _f), ("sw_succ", _i), ("sw_fail", _i), ("sw_step", _f * 3), ("batch_warps", _i)]
+                ("sw_contract", _f), ("sw_succ", _i), ("sw_fail", _i), ("sw_step", _f * 3), ("batch_warps", _i),
+                ("batch_pack", _i)]
 
 
 ALLOC_FN = C.CFUNCTYPE(_vp, _sz, _vp, _vp)

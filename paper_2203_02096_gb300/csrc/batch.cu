@@ -249,73 +249,108 @@ extern "C" int dock_batch(dock_ctx *ctx, const dock_grids *grids, const dock_lig
         P.ls_count > 256 || P.ls_iters < 0 || !(P.rho >= 0.f && P.rho < 1.f) || !(P.eps > 0.f))
         return set_err(ctx, DOCK_ERR_INVALID, "invalid dock_params");
     if (int rc0 = check_sw(ctx, P)) return rc0;
+    if (P.batch_pack != 0 && P.batch_pack != 1) return set_err(ctx, DOCK_ERR_INVALID, "batch_pack must be 0 or 1");
     cudaStream_t s = (cudaStream_t)stream;
-    size_t smem_per_warp = 0;
     std::vector<LigandDev> hl(n_ligs);
+    std::vector<size_t> need(n_ligs);  // shared-memory floats per warp of each ligand
     for (int k = 0; k < n_ligs; ++k) {
         if (!ligs[k]) return set_err(ctx, DOCK_ERR_INVALID, "null ligand");
         int rc = check_maps(ctx, grids, ligs[k]);
         if (rc) return rc;
         hl[k] = ligs[k]->dev;
         const LigandDev &L = hl[k];
-        const size_t need = (size_t)std::max(eval_layout(L.n_atoms, L.n_frag, L.nb8, true, 1).total,
-                                             eval_layout(L.n_atoms, L.n_frag, L.nb8, false, 1).total);
-        smem_per_warp = std::max(smem_per_warp, need);
+        need[k] = (size_t)std::max(eval_layout(L.n_atoms, L.n_frag, L.nb8, true, 1).total,
+                                   eval_layout(L.n_atoms, L.n_frag, L.nb8, false, 1).total);
+        if (need[k] * 4 > ctx->smem_optin) return set_err(ctx, DOCK_ERR_SIZE, "ligand too large for shared memory");
     }
-    if (smem_per_warp * 4 > ctx->smem_optin) return set_err(ctx, DOCK_ERR_SIZE, "ligand too large for shared memory");
-    // tasks: every run of every ligand, largest ligands first
+    // tasks: every run of every ligand, largest ligands first; with packing
+    // by atom count, cut into classes of at most 32, 64, 96, 128, 255 atoms
     std::vector<int> order(n_ligs);
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return hl[a].n_atoms > hl[b].n_atoms; });
     const int R = P.nruns, n_tasks = n_ligs * R;
+    auto size_class = [&](int k) {
+        const int n = hl[k].n_atoms;
+        return P.batch_pack == 0 ? 0 : n <= 32 ? 4 : n <= 64 ? 3 : n <= 96 ? 2 : n <= 128 ? 1 : 0;
+    };
+    struct Cls {
+        int t0, n;
+        size_t smem_per_warp;
+    };
+    std::vector<Cls> cls;
     std::vector<Task> tasks;
     tasks.reserve(n_tasks);
-    for (int k : order)
+    for (int k : order) {
+        if (cls.empty() || size_class(k) != size_class(tasks.back().lig))
+            cls.push_back(Cls{(int)tasks.size(), 0, 0});
         for (int r = 0; r < R; ++r) tasks.push_back(Task{k, r, k * R + r, seeds ? seeds[k] : (unsigned long long)k});
+        cls.back().n += R;
+        cls.back().smem_per_warp = std::max(cls.back().smem_per_warp, need[k]);
+    }
     const int gmax = 7 + DOCK_MAX_TORSIONS;
     const size_t floats_per_warp = ((2 * (size_t)P.pop_size * gmax + 3 * (size_t)P.pop_size + 63) / 64) * 64;
     // warps per block: as asked, else by shared-memory fit; blocks to fill every SM
     if (P.batch_warps != 0 && P.batch_warps != 1 && P.batch_warps != 2 && P.batch_warps != 4)
         return set_err(ctx, DOCK_ERR_INVALID, "batch_warps must be 0, 1, 2 or 4");
-    int wpb = P.batch_warps ? P.batch_warps : 4;
-    if (P.batch_warps && smem_per_warp * 4 * wpb > ctx->smem_optin)
-        return set_err(ctx, DOCK_ERR_SIZE, "batch_warps: the block's shared memory does not fit");
-    while (wpb > 1 && smem_per_warp * 4 * wpb > ctx->smem_optin) wpb >>= 1;
-    const size_t smem = smem_per_warp * 4 * wpb;
     const bool b3 = ctx->batch_min_blocks == 3;
     auto kern = P.ls_method == 1 ? (b3 ? lga_persistent<1, 3> : lga_persistent<1, 4>)
                                  : (b3 ? lga_persistent<0, 3> : lga_persistent<0, 4>);
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    struct Launch {
+        int blocks, wpb;
+        size_t smem;
+    };
+    std::vector<Launch> ln;
+    int max_warps = 0;
+    for (const Cls &c : cls) {
+        int wpb = P.batch_warps ? P.batch_warps : 4;
+        if (P.batch_warps && c.smem_per_warp * 4 * wpb > ctx->smem_optin)
+            return set_err(ctx, DOCK_ERR_SIZE, "batch_warps: the block's shared memory does not fit");
+        while (wpb > 1 && c.smem_per_warp * 4 * wpb > ctx->smem_optin) wpb >>= 1;
+        const size_t smem = c.smem_per_warp * 4 * wpb;
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e) return cuda_err(ctx, e, "dock_batch attributes");
+        }
+        int per_sm = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * wpb, smem);
+        if (e || per_sm < 1)
+            return e ? cuda_err(ctx, e, "dock_batch occupancy") : set_err(ctx, DOCK_ERR_SIZE, "no occupancy");
+        const int blocks = std::min(per_sm * ctx->num_sms, (c.n + wpb - 1) / wpb);
+        ln.push_back(Launch{blocks, wpb, smem});
+        max_warps = std::max(max_warps, blocks * wpb);
+    }
+    // the attribute must allow the largest block of any class
+    size_t smem_max = 0;
+    for (const Launch &l : ln) smem_max = std::max(smem_max, l.smem);
+    if (smem_max > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
         if (e) return cuda_err(ctx, e, "dock_batch attributes");
     }
-    int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * wpb, smem);
-    if (e || per_sm < 1) return e ? cuda_err(ctx, e, "dock_batch occupancy") : set_err(ctx, DOCK_ERR_SIZE, "no occupancy");
-    int blocks = per_sm * ctx->num_sms;
-    blocks = std::min(blocks, (n_tasks + wpb - 1) / wpb);
-    const int warps = blocks * wpb;
+    const int n_cls = (int)cls.size();
 
     const BatchConst BC = batch_const(P);
 
     LigandDev *d_ligs = (LigandDev *)dev_alloc(ctx, sizeof(LigandDev) * n_ligs, s);
     Task *d_tasks = (Task *)dev_alloc(ctx, sizeof(Task) * n_tasks, s);
-    int *d_next = (int *)dev_alloc(ctx, sizeof(int), s);
-    float *scratch = (float *)dev_alloc(ctx, floats_per_warp * 4 * warps, s);
+    int *d_next = (int *)dev_alloc(ctx, sizeof(int) * n_cls, s);
+    float *scratch = (float *)dev_alloc(ctx, floats_per_warp * 4 * max_warps, s);
     unsigned long long *d_ev = (unsigned long long *)dev_alloc(ctx, 8 * (size_t)n_tasks, s);
     float *bE32 = best_E32 ? best_E32 : (float *)dev_alloc(ctx, 4 * (size_t)n_tasks, s);
     int rc = DOCK_OK;
+    cudaError_t e = cudaSuccess;
     if (!d_ligs || !d_tasks || !d_next || !scratch || !d_ev || !bE32) {
         rc = set_err(ctx, DOCK_ERR_OOM, "device allocation failed in dock_batch");
     } else {
         e = cudaMemcpyAsync(d_ligs, hl.data(), sizeof(LigandDev) * n_ligs, cudaMemcpyHostToDevice, s);
         if (!e) e = cudaMemcpyAsync(d_tasks, tasks.data(), sizeof(Task) * n_tasks, cudaMemcpyHostToDevice, s);
-        if (!e) e = cudaMemsetAsync(d_next, 0, sizeof(int), s);
-        if (!e) {
+        if (!e) e = cudaMemsetAsync(d_next, 0, sizeof(int) * n_cls, s);
+        for (int c = 0; c < n_cls && !e; ++c) {
+            const Launch &l = ln[c];
             TimedLaunch tl;
             timing_begin(ctx, kernel_id(ctx, "dock_batch"), s, &tl);
-            kern<<<blocks, 32 * wpb, smem, s>>>(d_ligs, grids->dev, d_tasks, n_tasks, d_next, BC, scratch,
-                                               floats_per_warp, gmax, smem_per_warp, best_geno, bE32, d_ev);
+            kern<<<l.blocks, 32 * l.wpb, l.smem, s>>>(d_ligs, grids->dev, d_tasks + cls[c].t0, cls[c].n, d_next + c,
+                                                      BC, scratch, floats_per_warp, gmax, cls[c].smem_per_warp,
+                                                      best_geno, bE32, d_ev);
             timing_end(ctx, s, &tl);
             ++ctx->launches;
             e = cudaGetLastError();

@@ -146,6 +146,7 @@ void dock_default_params(dock_params *p) {
     p->sw_step[1] = 0.2f;
     p->sw_step[2] = 0.75f;
     p->batch_warps = 0;
+    p->batch_pack = 0;
 }
 
 int dock_create(dock_ctx **out, int device, const dock_allocator *alloc) {

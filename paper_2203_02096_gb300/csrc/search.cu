@@ -108,9 +108,10 @@ __global__ void picks_kernel(int pop, int n_ls, int nruns, uint2 key, uint32_t g
 // in the population; without: chain c starts at x_in[c] and writes x_out[c].
 // trace (x, g, E null inside dock): chain c records its iterations at
 // x + c iters G, g + c iters G, E + c iters.
-// Residency: W = 8 keeps 3 blocks (24 warps) per SM, W = 4 four, W = 2 eight.
+// Residency: W = 8 keeps 3 blocks (24 warps) per SM, W = 4 three (168
+// registers: the chains of a docking are too few to fill more), W = 2 six.
 template <int W>
-__global__ void __launch_bounds__(W == 1 ? 128 : 32 * W, W == 8 ? 3 : W == 4 ? 4 : W == 2 ? 8 : 4)
+__global__ void __launch_bounds__(W == 1 ? 128 : 32 * W, W == 8 ? 3 : W == 4 ? 3 : W == 2 ? 6 : 4)
 ls_kernel(LigandDev L, GridDev G, float *x_in, float *E_pop, const int *__restrict__ picks, int pop, int n_ls,
           int nchains, int iters, float rho, float eps, float *x_out, float *E_out, unsigned long long *evals,
           EvalLayout Y, LsTrace trace) {
@@ -341,8 +342,11 @@ int ls_team_warps(const dock_ctx *ctx, int chains, int threads_req, const Ligand
     if (threads_req > 0) {
         w = threads_req / 32;
     } else {
+        // ... and only while all chains stay resident at once (teams per SM
+        // as ls_kernel's launch bounds allow: 6 two-warp, 3 four- or eight-warp)
         const long long target = 16LL * ctx->num_sms;
-        while (w < 8 && (long long)chains * 2 * w <= target) w <<= 1;
+        auto resident = [&](int tw) { return (long long)(tw == 2 ? 6 : 3) * ctx->num_sms; };
+        while (w < 8 && (long long)chains * 2 * w <= target && chains <= resident(2 * w)) w <<= 1;
     }
     w = w >= 8 ? 8 : w >= 4 ? 4 : w >= 2 ? 2 : 1;
     while (w > 1 && (size_t)eval_layout(L.n_atoms, L.n_frag, L.nb8, true, w).total * 4 > ctx->smem_optin) w >>= 1;

@@ -51,3 +51,21 @@ def test_batch_equals_per_ligand_docking_and_is_mix_independent(gpu, drug_system
         olig = oracle_mod.OracleLigand(ligs[k])
         ref = olig.score_batch(ogrid, bg[k, :, :L[k].n_genes], with_grad=False)
         assert np.allclose(bE[k], ref, rtol=1e-9, atol=1e-9)
+
+
+def test_packing_by_atom_count_changes_nothing(gpu, drug_system):
+    """batch_pack = 1 (one launch per atom-count class, each sized for its own
+    largest ligand) gives the same results, bit for bit, as one launch."""
+    ligs = _ligands(14, 5) + [synth.make_ligand(20, 3, seed=77), synth.make_ligand(120, 20, seed=78)]
+    L = [capi.ligand_from(gpu, l) for l in ligs]
+    G = capi.grids_from_maps(gpu, drug_system["maps"], drug_system["box"])
+    seeds = np.arange(len(L), dtype=np.uint64) * 31 + 5
+    outs = []
+    for pack in (0, 1):
+        P = capi.default_params(pop_size=40, nruns=2, max_evals=1500, ls_iters=10, batch_pack=pack)
+        outs.append(capi.dock_batch(gpu, G, L, P, seeds))
+    torch.cuda.synchronize()
+    for k in ("best_geno", "best_E32", "best_E", "evals"):
+        assert torch.equal(outs[0][k], outs[1][k]), k
+    with pytest.raises(capi.DockError, match="INVALID"):
+        capi.dock_batch(gpu, G, L[:2], capi.default_params(batch_pack=2), seeds[:2])
