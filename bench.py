@@ -141,6 +141,27 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
+# synthetic ligands in parallel (spawned worker processes, which touch no GPU)
+
+def _ligand_worker(spec):
+    from paper_2203_02096_gb300 import synth
+    n, t, seed = spec
+    return synth.make_ligand(n, t, seed=seed)
+
+
+def make_ligands(specs):
+    """synth.make_ligand(n, t, seed=seed) for each (n, t, seed), in order."""
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    specs = list(specs)
+    workers = min(len(specs), os.cpu_count() or 1)
+    if workers <= 1:
+        return [_ligand_worker(sp) for sp in specs]
+    with ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(_ligand_worker, specs, chunksize=max(1, len(specs) // (4 * workers))))
+
+
+# ---------------------------------------------------------------------------
 # the workload
 
 def workload():
@@ -307,16 +328,27 @@ def run(args):
     e2e_s = max_over_ranks(time.perf_counter() - t0, dev)
     e2e_value = sum_over_ranks(float(e2e_evals), dev) / e2e_s
 
-    batch = score_grad_throughput(ctx, G, w.box, dev) if not args.no_batch else None
-    multi = batched_docking(ctx, dev) if not args.no_batch else None
-    serving = serving_sweep(ctx, dev) if not args.no_batch else None
-    solis = solis_wets_vs_adadelta(ctx, G, L, w, dev, out, value) if not args.no_batch else None
-    tuning = tuning_curves(ctx, G, w, tuner, P) if not args.no_batch else None
+    section_s = {}
+
+    def side(name, fn):
+        t = time.perf_counter()
+        r = fn() if not args.no_batch else None
+        section_s[name] = round(time.perf_counter() - t, 1)
+        print(f"[bench] {name}: {section_s[name]} s", file=sys.stderr, flush=True)
+        return r
+
+    batch = side("score_grad_batch", lambda: score_grad_throughput(ctx, G, w.box, dev))
+    multi = side("batched_docking", lambda: batched_docking(ctx, dev, full=not args.quick))
+    serving = side("serving", lambda: serving_sweep(ctx, dev, full=not args.quick))
+    solis = side("solis_wets", lambda: solis_wets_vs_adadelta(ctx, G, L, w, dev, out, value))
+    tuning = side("tuning", lambda: tuning_curves(ctx, G, w, tuner, P))
 
     cpu = None
     if rank == 0 and not args.no_cpu:
+        t = time.perf_counter()
         v, cores, desc, _ = cpu_sample(w, args.cpu_seconds)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+        section_s["cpu_baseline"] = round(time.perf_counter() - t, 1)
 
     if rank == 0:
         line = {
@@ -351,6 +383,7 @@ def run(args):
             "solis_wets": solis,
             "tuning": tuning,
             "best_energy_median": float(np.median(out["best_E"].cpu().numpy())),
+            "side_section_seconds": section_s,
         }
         print(json.dumps(line), flush=True)
     for h in (L, G):
@@ -452,118 +485,194 @@ def run_batch_small() -> int:
     return 0
 
 
-def batched_docking(ctx, dev, n_ligs: int = 1024, nruns: int = 20, evals_per_run: int = 20_000,
-                    full_budget: int = 1_000_000, n_plain: int = 12):
-    """Many-ligand docking in one persistent launch (dock_batch) against the
-    plain per-ligand form (dock, one launch sequence per ligand): 1024
-    ligands with 10-108 atoms and 0-32 torsions, 20 runs each, 80^3 x 9 maps.
-    Both run each docking run with a reduced budget; ligands/hour at the full
-    1M-evaluation budget is extrapolated from evals/s (the cost per
-    evaluation does not depend on the budget)."""
+def batched_docking(ctx, dev, n_ligs: int = 1024, nruns: int = 20, full_budget: int = 1_000_000,
+                    probe_budget: int = 20_000, n_plain: int = 32, full: bool = True):
+    """The batching workload: 1024 ligands with 10-108 atoms and 0-32
+    torsions, 20 runs each, 80^3 x 9 maps, docked in one persistent launch
+    (dock_batch), against the plain per-ligand form (dock, one launch
+    sequence per ligand) on the same GPU.
+    - packing: both packing modes (one largest-first launch; one launch per
+      atom-count class) at the default and the autotuned launch shape, on
+      the whole batch at probe_budget evaluations per run;
+    - full budget (1M evaluations per run): the whole batch in one launch,
+      and the plain form on n_plain ligands spread evenly over the size
+      range, with the best energies of those ligands' runs in both forms
+      (equal budget, same seeds): throughput and quality, not extrapolated."""
     import torch
 
     from paper_2203_02096_gb300 import autotune, capi, synth
     rng = np.random.default_rng(3)
-    ligs = [synth.make_ligand(int(rng.integers(10, 109)), int(rng.integers(0, 33)), seed=5000 + k)
-            for k in range(n_ligs)]
+    ligs = make_ligands([(int(rng.integers(10, 109)), int(rng.integers(0, 33)), 5000 + k) for k in range(n_ligs)])
     box = synth.make_box(80)
     G = capi.grids_from_receptor(ctx, synth.make_receptor(3000, seed=4), box)
     L = [capi.ligand_from(ctx, l) for l in ligs]
-    P = capi.default_params(pop_size=150, nruns=nruns, max_evals=evals_per_run, ls_iters=100)
     seeds = np.arange(n_ligs, dtype=np.uint64)
-    # warps per block of the persistent kernel by the autotuner (one-generation probes)
+    P = capi.default_params(pop_size=150, nruns=nruns, max_evals=probe_budget, ls_iters=100)
+    # warps per block and register cap of the persistent kernel by the autotuner (one-generation probes)
     tuner = autotune.Tuner(ctx, path=os.path.join(tempfile.mkdtemp(prefix="dock_tune_"), "tune.json"))
-    Pb = capi.DockParams.from_buffer_copy(P)
-    Pb.batch_warps = tuner.batch_warps(G, L, P, probe_generations=1)
-    batch_blocks = tuner.batch_blocks(G, L, Pb, probe_generations=1)   # register cap, set on the context
-    capi.dock_batch(ctx, G, L[:8], Pb, seeds[:8])          # warm-up
+    tuned_warps = tuner.batch_warps(G, L, P, probe_generations=1)
+    Pt = capi.DockParams.from_buffer_copy(P)
+    Pt.batch_warps = tuned_warps
+    tuned_blocks = tuner.batch_blocks(G, L, Pt, probe_generations=1)
+
+    def timed_batch(params, blocks):
+        capi.set_option(ctx, capi.OPT_BATCH_BLOCKS, blocks)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        out = capi.dock_batch(ctx, G, L, params, seeds)
+        b.record()
+        torch.cuda.synchronize(dev)
+        return a.elapsed_time(b) / 1e3, out
+
+    capi.dock_batch(ctx, G, L[:8], Pt, seeds[:8])          # warm-up
     torch.cuda.synchronize(dev)
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record()
-    out = capi.dock_batch(ctx, G, L, Pb, seeds)
-    b.record()
-    torch.cuda.synchronize(dev)
-    t_batch = a.elapsed_time(b) / 1e3
-    ev_batch = int(out["evals"].sum().item())
-    # plain form on a sample of the same ligands, one docking at a time
-    ev_plain = 0
-    plain_params = [tuner.tuned(G, L[k], P) for k in range(n_plain)]   # threads per chain, per ligand
-    torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    for k in range(n_plain):
-        _, _, ev = capi.dock(ctx, G, L[k], plain_params[k], int(seeds[k]))
-        ev_plain += int(ev.sum())
-    torch.cuda.synchronize(dev)
-    t_plain = time.perf_counter() - t0
+    packing = []
+    for shape, warps, blocks in (("default", 4, 4), ("autotuned", tuned_warps, tuned_blocks)):
+        for pack in (0, 1):
+            Pp = capi.DockParams.from_buffer_copy(P)
+            Pp.batch_warps, Pp.batch_pack = warps, pack
+            t, out = timed_batch(Pp, blocks)
+            packing.append({"shape": shape, "batch_warps": int(warps), "batch_blocks": int(blocks),
+                            "pack": "by atom count" if pack else "one launch, largest first",
+                            "seconds": t, "evals_per_s": float(out["evals"].sum().item()) / t})
+    best = min(packing, key=lambda r: r["seconds"])
+    res = {"workload": f"{n_ligs} ligands (10-108 atoms, 0-32 torsions), {nruns} runs, pop 150, 80^3 x 9 maps",
+           "packing": {"budget_per_run": probe_budget, "runs": packing},
+           "autotuned": {"batch_warps": int(tuned_warps), "batch_warps_ms": tuner.curve("|batch|"),
+                         "batch_blocks": int(tuned_blocks), "batch_blocks_ms": tuner.curve("|batchregs|")}}
+    if full:
+        Pf = capi.DockParams.from_buffer_copy(P)
+        Pf.max_evals = full_budget
+        Pf.batch_warps = best["batch_warps"]
+        Pf.batch_pack = 1 if best["pack"] == "by atom count" else 0
+        t_batch, out = timed_batch(Pf, best["batch_blocks"])
+        ev_batch = int(out["evals"].sum().item())
+        bE = out["best_E"].cpu().numpy()
+        # plain form: n_plain ligands spread over the size range, one docking at a time
+        by_size = np.argsort([l.n_atoms for l in ligs], kind="stable")
+        pick = by_size[np.linspace(0, n_ligs - 1, n_plain).round().astype(int)]
+        # 128 threads per local-search chain: the autotuner's choice for the
+        # 21-, 43- and 108-atom ligands of the tuning curves
+        Pplain = capi.DockParams.from_buffer_copy(Pf)
+        Pplain.ls_threads = 128
+        torch.cuda.synchronize(dev)
+        ev_plain, pE = 0, []
+        t0 = time.perf_counter()
+        for k in pick:
+            _, e, ev = capi.dock(ctx, G, L[k], Pplain, int(seeds[k]))
+            ev_plain += int(ev.sum())
+            pE.append(e)
+        torch.cuda.synchronize(dev)
+        t_plain = time.perf_counter() - t0
+        pE = np.array(pE)
+        t_batch_pick = t_batch * ev_plain / ev_batch   # the batch's time share of those ligands' evaluations
+        res["full_budget"] = {
+            "budget_per_run": full_budget, "shape": {k: best[k] for k in ("batch_warps", "batch_blocks", "pack")},
+            "batch_seconds": t_batch, "batched_evals_per_s": ev_batch / t_batch,
+            "batched_ligands_per_hour": 3600.0 * n_ligs / t_batch,
+            "plain_ligands": int(n_plain), "plain_seconds": t_plain, "plain_evals_per_s": ev_plain / t_plain,
+            "plain_ligands_per_hour": 3600.0 * n_plain / t_plain,
+            "speedup_evals_per_s": (ev_batch / t_batch) / (ev_plain / t_plain),
+            "best_E_median": {"batched": float(np.median(bE[pick])), "plain": float(np.median(pE))},
+            "best_E_median_all_1024": float(np.median(bE)),
+            "per_ligand_median_diff": float(np.median(np.median(bE[pick], axis=1) - np.median(pE, axis=1))),
+            "plain_ls_threads": 128,
+            "note": f"plain form timed on {n_plain} of the ligands (every {n_ligs // n_plain}th by atom count); "
+                    f"equal budget and seeds in both forms; batched time share of those ligands ~{t_batch_pick:.1f} s"}
     for h in L + [G]:
         h.free()
     capi.set_option(ctx, capi.OPT_BATCH_BLOCKS, 4)
-    rate_b, rate_p = ev_batch / t_batch, ev_plain / t_plain
-    per_lig_full = nruns * full_budget
-    return {"workload": f"{n_ligs} ligands (10-108 atoms, 0-32 torsions), {nruns} runs, pop 150, 80^3 x 9 maps",
-            "sample": f"{evals_per_run} evaluations per run (full budget {full_budget}); plain form timed on "
-                      f"{n_plain} of the ligands",
-            "batched_evals_per_s": rate_b, "plain_evals_per_s": rate_p, "speedup": rate_b / rate_p,
-            "batched_ligands_per_hour_extrapolated": 3600.0 * rate_b / per_lig_full,
-            "plain_ligands_per_hour_extrapolated": 3600.0 * rate_p / per_lig_full,
-            "batch_seconds": t_batch, "launches": 1,
-            "autotuned": {"batch_warps": int(Pb.batch_warps), "batch_warps_ms": tuner.curve("|batch|"),
-                          "batch_blocks": int(batch_blocks), "batch_blocks_ms": tuner.curve("|batchregs|"),
-                          "plain_ls_threads": [int(p.ls_threads) for p in plain_params]}}
+    return res
 
 
-def serving_sweep(ctx, dev, rates=(10, 30, 100, 300, 1000), seconds: float = 2.0, nruns: int = 20,
-                  evals_per_run: int = 5_000, full_budget: int = 500_000, n_plain: int = 8):
-    """Continuous-batching service (server_* + serve.run): Poisson arrivals
-    of ligands with 10-128 atoms (log-uniform) and 0-32 torsions against two
-    receptors with 96^3 x 9 maps, 20 runs per request; p50/p99 latency and
-    throughput per arrival rate, beside the plain form (one dock() call per
-    request, in arrival order).  Each run gets evals_per_run evaluations
-    (full budget 500k: latencies scale with it, the ordering does not)."""
+def serving_sweep(ctx, dev, full_budget: int = 500_000, full_rates=((10, 30.0), (30, 8.0)),
+                  probe_rates=(10, 30, 100, 300, 1000), probe_budget: int = 5_000, probe_seconds: float = 2.0,
+                  nruns: int = 20, n_plain: int = 8, full: bool = True):
+    """The serving workload: Poisson arrivals of ligands with 10-128 atoms
+    (log-uniform) and 0-32 torsions against two receptors with 96^3 x 9
+    maps, 20 runs per request, through the continuous-batching server
+    (server_* + serve.run).
+    - full budget (500k evaluations per run): arrival rates 10 and 30 per
+      second for the stated seconds of arrivals; p50/p99 latency (arrival to
+      all runs done), throughput, ligands/hour, and whether the rate is past
+      saturation (served rate while requests still arrive below 80% of the
+      arrival rate); the plain
+      form (one dock() per request, in order) on the first n_plain requests
+      of the rate-10 stream, with the best energies of the same requests in
+      both forms;
+    - the knee at a reduced budget: every probe rate for probe_seconds."""
     import torch
 
     from paper_2203_02096_gb300 import capi, serve, synth
     centers = [(12.5, -3.25, 7.0), (-30.0, 18.0, 4.0)]
     grids = [capi.grids_from_receptor(ctx, synth.make_receptor(3000, center=c, seed=11 + i), synth.make_box(96, center=c))
              for i, c in enumerate(centers)]
-    P = capi.default_params(pop_size=150, nruns=nruns, max_evals=evals_per_run, ls_iters=100)
     server = capi.Server(ctx, capacity=1 << 16, max_atoms=128, pop_max=150)
+    # request k of every stream: the same ligand (sizes from one seeded draw)
+    n_req = max([max(8, int(r * t)) for r, t in full_rates] + [max(8, int(r * probe_seconds)) for r in probe_rates])
     rng = np.random.default_rng(17)
-
-    def request(k):
+    specs = []
+    for k in range(n_req):
         n = int(np.exp(rng.uniform(np.log(10), np.log(128.999))))
-        return serve.Request(synth.make_ligand(n, int(rng.integers(0, 33)), seed=9000 + k), k % 2, seed=k)
+        specs.append((n, int(rng.integers(0, 33)), 9000 + k))
+    req_ligs = make_ligands(specs)
 
-    # warm-up: one request through the server
-    serve.run(ctx, server, grids, [request(0)], P)
-    out = []
-    for rate in rates:
+    def stream(rate, seconds, budget, seed):
         n = max(8, int(rate * seconds))
-        reqs = [request(k) for k in range(n)]
-        for r, t in zip(reqs, serve.poisson_arrivals(n, rate, seed=int(rate))):
+        reqs = [serve.Request(req_ligs[k], k % 2, seed=k) for k in range(n)]
+        for r, t in zip(reqs, serve.poisson_arrivals(n, rate, seed=seed)):
             r.arrival = float(t)
-        rep = serve.run(ctx, server, grids, reqs, P)
-        out.append(dict(rate_per_s=rate, **rep.summary()))
-    # the plain form: one docking at a time
-    reqs = [request(k) for k in range(n_plain)]
-    t0 = time.perf_counter()
-    lat = []
-    for r in reqs:
-        ts = time.perf_counter()
-        L = capi.ligand_from(ctx, r.ligand)
-        capi.dock(ctx, grids[r.grid_index], L, P, r.seed)
-        L.free()
-        lat.append(time.perf_counter() - ts)
-    t_plain = time.perf_counter() - t0
+        return reqs
+
+    res = {"workload": "ligands 10-128 atoms (log-uniform), 0-32 torsions, 20 runs, 2 receptors x 96^3 x 9 maps"}
+    # warm-up: one request through the server
+    Pw = capi.default_params(pop_size=150, nruns=nruns, max_evals=probe_budget, ls_iters=100)
+    serve.run(ctx, server, grids, stream(10, 0.1, probe_budget, 0)[:1], Pw)
+    if full:
+        P = capi.default_params(pop_size=150, nruns=nruns, max_evals=full_budget, ls_iters=100)
+        sweep, first = [], None
+        for rate, seconds in full_rates:
+            reqs = stream(rate, seconds, full_budget, int(rate))
+            rep = serve.run(ctx, server, grids, reqs, P, timeout=900.0)
+            sm = rep.summary()
+            st = sm["steady_throughput_per_s"]
+            sm["saturated"] = None if st is None else bool(st < 0.8 * rate)
+            sweep.append(dict(rate_per_s=rate, arrival_seconds=seconds, **sm))
+            if first is None:
+                first = {d.request.seed: d for d in rep.done}
+                first_reqs = reqs
+        # plain form on the first requests of the first stream
+        lat, pE, sE = [], [], []
+        t0 = time.perf_counter()
+        for r in first_reqs[:n_plain]:
+            ts = time.perf_counter()
+            Lr = capi.ligand_from(ctx, r.ligand)
+            _, e, _ = capi.dock(ctx, grids[r.grid_index], Lr, P, r.seed)
+            Lr.free()
+            lat.append(time.perf_counter() - ts)
+            pE.append(e)
+            sE.append(first[r.seed].best_E)
+        t_plain = time.perf_counter() - t0
+        res["full_budget"] = {
+            "budget_per_run": full_budget, "sweep": sweep,
+            "plain": {"requests": n_plain, "requests_per_s": n_plain / t_plain,
+                      "ligands_per_hour": 3600.0 * n_plain / t_plain, "latency_s_median": float(np.median(lat))},
+            "best_E_median_same_requests": {"served": float(np.median(sE)), "plain": float(np.median(pE))}}
+    # the knee at a reduced budget
+    Pp = capi.default_params(pop_size=150, nruns=nruns, max_evals=probe_budget, ls_iters=100)
+    knee = []
+    for rate in probe_rates:
+        rep = serve.run(ctx, server, grids, stream(rate, probe_seconds, probe_budget, int(rate) + 1), Pp)
+        sm = rep.summary()
+        st = sm["steady_throughput_per_s"]
+        sm["saturated"] = None if st is None else bool(st < 0.8 * rate)
+        knee.append(dict(rate_per_s=rate, **sm))
+    res["reduced_budget"] = {"budget_per_run": probe_budget, "arrival_seconds": probe_seconds, "sweep": knee}
     server.close()
     for g in grids:
         g.free()
     torch.cuda.synchronize(dev)
-    return {"workload": "ligands 10-128 atoms (log-uniform), 0-32 torsions, 20 runs, 2 receptors x 96^3 x 9 maps",
-            "sample": f"{evals_per_run} evaluations per run (full budget {full_budget}); {seconds} s of arrivals per rate",
-            "sweep": out,
-            "plain": {"requests_per_s": n_plain / t_plain, "ligands_per_hour": 3600.0 * n_plain / t_plain,
-                      "latency_s_median": float(np.median(lat))}}
+    return res
 
 
 def tuning_curves(ctx, G, w, tuner, P_head):
@@ -690,7 +799,9 @@ def main(argv=None):
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--no-batch", action="store_true", help="skip the score_grad_batch side measurement")
+    ap.add_argument("--no-batch", action="store_true", help="skip the side measurements")
+    ap.add_argument("--quick", action="store_true",
+                    help="side measurements without the full-budget batching and serving runs")
     ap.add_argument("--ls-threads", type=int, default=-1,
                     help="threads per local-search chain (-1 = autotuned, 0 = library default)")
     ap.add_argument("--only", choices=["score_grad", "batch_small"], default=None,

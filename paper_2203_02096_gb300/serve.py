@@ -47,10 +47,26 @@ class ServiceReport:
     def latencies(self) -> np.ndarray:
         return np.array([d.latency for d in self.done])
 
+    def steady_throughput(self):
+        """Completions per second while requests were still arriving (from
+        the first completion to the last arrival), or None when that window
+        is under a second: the served rate without the ramp-up and drain of
+        a finite stream."""
+        if not self.done:
+            return None
+        finish = np.sort([d.request.arrival + d.latency for d in self.done])
+        last_arrival = max(d.request.arrival for d in self.done)
+        t1 = finish[0]
+        if last_arrival - t1 < 1.0:
+            return None
+        n = int(np.searchsorted(finish, last_arrival, side="right")) - 1
+        return n / (last_arrival - t1)
+
     def summary(self) -> dict:
         lat = self.latencies()
         return {"requests": len(self.done), "wall_s": self.wall,
                 "throughput_per_s": len(self.done) / self.wall if self.wall > 0 else 0.0,
+                "steady_throughput_per_s": self.steady_throughput(),
                 "ligands_per_hour": 3600.0 * len(self.done) / self.wall if self.wall > 0 else 0.0,
                 "p50_s": float(np.percentile(lat, 50)) if len(lat) else None,
                 "p99_s": float(np.percentile(lat, 99)) if len(lat) else None,

@@ -89,6 +89,55 @@ def _unit(rng):
     return v / np.linalg.norm(v)
 
 
+def _place_one_by_one(rng, origin, others, need):
+    """Draw directions one at a time until the new atom keeps every required
+    distance (slack >= 0), at most PLACE_TRIES times; keep the least crowded
+    (first of the largest slack)."""
+    best, best_slack = None, -np.inf
+    for _ in range(PLACE_TRIES):
+        p = origin + BOND_LENGTH * _unit(rng)
+        slack = float(np.min(np.linalg.norm(others - p, axis=1) - need))
+        if slack > best_slack:
+            best, best_slack = p, slack
+        if slack >= 0.0:
+            break
+    return best
+
+
+def _place(rng, origin, others, need):
+    """_place_one_by_one, with the tries screened all at once: the candidate
+    directions are drawn as one block from a copy of the generator's state,
+    the try the one-by-one loop would stop at is found from all slacks, and
+    the generator is then advanced by exactly the draws that loop makes.
+    Where rounding could decide the outcome (a slack within 1e-9 of zero, or
+    of the best slack), the one-by-one loop itself runs instead.  Same
+    directions, same atom, same generator state afterwards."""
+    state = rng.bit_generator.state
+    v = rng.standard_normal((PLACE_TRIES, 3))
+    p = origin + BOND_LENGTH * (v / np.sqrt(np.einsum("ij,ij->i", v, v))[:, None])
+
+    def slacks(rows):
+        d = np.sqrt(((p[rows, None, :] - others[None, :, :]) ** 2).sum(axis=2))
+        return (d - need).min(axis=1)
+
+    slack = slacks(slice(0, 16))          # most atoms fit within the first few tries
+    if not (slack >= 0.0).any():
+        slack = np.concatenate([slack, slacks(slice(16, PLACE_TRIES))])
+    ok = np.nonzero(slack >= 0.0)[0]
+    i = int(ok[0]) if ok.size else int(np.argmax(slack))
+    top = slack[i]
+    close = np.abs(slack[: i + 1]) < 1e-9 if ok.size else np.abs(slack) < 1e-9
+    if ok.size == 0:
+        close |= np.abs(slack - top) < 1e-9
+        close[i] = False
+    rng.bit_generator.state = state
+    if close.any():
+        return _place_one_by_one(rng, origin, others, need)
+    rng.standard_normal(((i + 1) if ok.size else PLACE_TRIES, 3))
+    w = v[i]
+    return origin + BOND_LENGTH * (w / np.linalg.norm(w))
+
+
 def make_ligand(n_atoms: int, n_torsions: int, type_names=TYPE_NAMES, seed: int = 0) -> Ligand:
     """Random tree ligand: atom k bonds to a uniformly chosen earlier atom of
     valence < 4, 1.5 A away in a random direction.  The direction is redrawn
@@ -111,15 +160,7 @@ def make_ligand(n_atoms: int, n_torsions: int, type_names=TYPE_NAMES, seed: int 
         parent = int(cand[rng.integers(len(cand))])
         hk = hops[parent, :k] + 1
         need = np.where(hk <= 1, 0.0, np.where(hk <= 3, MIN_13, MIN_15))
-        best, best_slack = None, -np.inf
-        for _ in range(PLACE_TRIES):
-            p = xyz[parent] + BOND_LENGTH * _unit(rng)
-            slack = float(np.min(np.linalg.norm(xyz[:k] - p, axis=1) - need))
-            if slack > best_slack:
-                best, best_slack = p, slack
-            if slack >= 0.0:
-                break
-        xyz[k] = best
+        xyz[k] = _place(rng, xyz[parent], xyz[:k], need)
         hops[k, :k] = hk
         hops[:k, k] = hk
         bonds.append((parent, k))

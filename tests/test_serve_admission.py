@@ -125,3 +125,20 @@ def test_a_request_larger_than_the_budget_runs_alone(fake_capi):
     assert [d.request.ligand["name"] for d in rep.done] == [0, 1, 2]
     assert srv.order == [0, 1, 2]
     assert FakeLigand.live == 0
+
+
+def test_steady_throughput_counts_completions_while_requests_arrive():
+    """Served rate without ramp-up and drain: 1 request/s arriving for 20 s,
+    each done 5 s after it arrives -> completions at 5..24 s, of which those
+    in [5, 19] (first completion to last arrival) give 14 in 14 s."""
+    from paper_2203_02096_gb300 import serve
+    rep = serve.ServiceReport()
+    for k in range(20):
+        r = serve.Request(ligand=None, grid_index=0, seed=k, arrival=float(k))
+        rep.done.append(serve.Done(r, 5.0, None, None, None))
+    rep.wall = 24.0
+    assert rep.steady_throughput() == pytest.approx(14 / 14)
+    assert rep.summary()["throughput_per_s"] == pytest.approx(20 / 24)
+    # a stream shorter than a second of overlap has no steady rate
+    short = serve.ServiceReport(done=rep.done[:1], wall=5.0)
+    assert short.steady_throughput() is None
