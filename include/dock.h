@@ -284,8 +284,9 @@ int dock_microbench(dock_ctx *ctx, int what, double *value);
  * (one ligand, its grids, params and seed) becomes nruns tasks; warps of the
  * running kernel pick tasks up as soon as they are submitted, so requests of
  * different sizes arriving while others run share the GPU at once.  The
- * queue lives in mapped host memory; idle warps poll it with a bounded wait
- * and leave after about a second without work; server_submit and
+ * queue lives in mapped host memory; idle warps poll it with a bounded wait.
+ * After about a second with no task in progress the launch winds down as a
+ * whole (every warp leaves and none claims again); server_submit and
  * server_poll relaunch the kernel when tasks are pending and none runs.  A
  * task's result depends only on its ligand, grids, params, seed and run
  * index (the same as dock_batch for them), not on what else is queued.

@@ -13,6 +13,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <chrono>
 #include <numeric>
 #include <string.h>
 #include <vector>
@@ -406,8 +407,10 @@ struct ServeDev {
     unsigned long long head;         // next task to claim
     unsigned long long tail;         // copy of the host's published tail
     unsigned long long last_read;    // globaltimer of the last host read
-    unsigned long long last_active;  // globaltimer of the last claim
+    unsigned long long last_active;  // globaltimer of the last claim or completion
     unsigned long long stop;         // copy of the host's stop flag
+    unsigned long long closing;      // set once the launch winds down: no warp claims any more
+    unsigned long long busy;         // tasks claimed and not yet completed
 };
 
 constexpr long long kMaxPolls = 100000000;
@@ -449,10 +452,11 @@ lga_serve(const volatile ServeTask *tasks, const volatile ServeCtl *ctl, int cap
             volatile ServeDev *vq = q;
             const unsigned long long idle0 = globaltimer_ns();
             for (long long polls = 0;; ++polls) {
-                if (vq->stop) break;
+                if (vq->stop || vq->closing) break;
                 const long long h = (long long)vq->head;
                 if (h < (long long)vq->tail) {
                     if ((long long)atomicCAS(&q->head, (unsigned long long)h, (unsigned long long)(h + 1)) == h) {
+                        atomicAdd(&q->busy, 1ull);
                         atomicMax(&q->last_active, globaltimer_ns());
                         t = h;
                         break;
@@ -465,10 +469,17 @@ lga_serve(const volatile ServeTask *tasks, const volatile ServeCtl *ctl, int cap
                     atomicMax(&q->tail, (unsigned long long)ctl->tail);
                     continue;
                 }
-                // bounded: once no warp has claimed a task for max_idle_ns every
-                // warp leaves, and the poll cap bounds the wait on its own
+                // bounded: once no task has been in progress for max_idle_ns the
+                // launch winds down -- every warp leaves, none claims again, so
+                // it ends at once and the host relaunches it for new work (a
+                // launch with most warps gone would otherwise keep the few
+                // left alive on new tasks and never end); the poll cap bounds
+                // the wait on its own
                 const unsigned long long act = max(idle0, vq->last_active);
-                if ((now > act && now - act > max_idle_ns) || polls >= kMaxPolls) break;
+                if ((vq->busy == 0 && now > act && now - act > max_idle_ns) || polls >= kMaxPolls) {
+                    atomicExch(&q->closing, 1ull);
+                    break;
+                }
                 __nanosleep(1000);
             }
         }
@@ -506,6 +517,8 @@ lga_serve(const volatile ServeTask *tasks, const volatile ServeCtl *ctl, int cap
             evals[out] = (unsigned long long)ev;
             __threadfence_system();
             done[out] = t + 1;  // completion: the task's sequence number
+            atomicMax(&q->last_active, globaltimer_ns());
+            atomicAdd(&q->busy, ~0ull);  // - 1
         }
         __syncwarp();
     }
@@ -534,6 +547,10 @@ struct dock_server {
     long long submitted = 0;
     cudaEvent_t running = nullptr;  // recorded after each launch
     bool launched = false;
+    // when server_poll last asked whether the kernel still runs: polls in
+    // between trust the answer (querying the launch's event hundreds of
+    // thousands of times a second was measured to slow the running kernel)
+    std::chrono::steady_clock::time_point last_check{};
 };
 
 extern "C" {
@@ -611,7 +628,11 @@ int server_create(dock_ctx *ctx, int capacity, int max_atoms, int pop_max, dock_
 static int server_kick(dock_server *S) {
     if (S->launched && cudaEventQuery(S->running) == cudaErrorNotReady) return DOCK_OK;
     cudaGetLastError();
-    const unsigned long long max_idle = 1000000000ull;  // the kernel ends after a second without claims
+    const unsigned long long max_idle = 1000000000ull;  // the kernel ends after a second with no task in progress
+    // the previous launch (if any) has ended: stream order puts this clear
+    // after it and before the new launch
+    cudaError_t e0 = cudaMemsetAsync(&S->q->closing, 0, sizeof(unsigned long long), S->stream);
+    if (e0) return cuda_err(S->ctx, e0, "server launch");
     S->kernel<<<S->blocks, 32 * S->wpb, S->smem, S->stream>>>(
         S->d_tasks, S->d_ctl, S->capacity, S->q, S->scratch, S->floats_per_warp, S->pop_max, S->smem_per_warp,
         S->best_geno, S->best_E32, S->best_E, S->evals, S->d_done, max_idle);
@@ -671,8 +692,12 @@ int server_poll(dock_server *S, int64_t first_task, int nruns, int *done) {
         all = *(volatile long long *)&S->done[t % S->capacity] == t + 1;
     }
     *done = all;
-    if (!all) return server_kick(S);  // keep the kernel alive while work is pending
-    return DOCK_OK;
+    if (all) return DOCK_OK;
+    // keep the kernel alive while work is pending, checking at most every ms
+    const auto now = std::chrono::steady_clock::now();
+    if (now - S->last_check < std::chrono::milliseconds(1)) return DOCK_OK;
+    S->last_check = now;
+    return server_kick(S);
 }
 
 int server_cancel(dock_server *S, int64_t first_task, int nruns) {

@@ -79,7 +79,7 @@ def poisson_arrivals(n: int, rate: float, seed: int = 0) -> np.ndarray:
 
 
 def run(ctx: capi.Context, server: capi.Server, grids: list, requests: list, params: capi.DockParams,
-        mem_budget: int = 2 << 30, poll_sleep: float = 2e-4, timeout: float = 600.0) -> ServiceReport:
+        mem_budget: int = 2 << 30, poll_sleep: float = 2e-3, timeout: float = 600.0) -> ServiceReport:
     """Serve ``requests`` (their ``arrival`` times set) until all are done."""
     pending = deque(sorted(requests, key=lambda r: r.arrival))
     waiting = deque()          # arrived, not yet admitted
