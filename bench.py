@@ -485,6 +485,75 @@ def run_batch_small() -> int:
     return 0
 
 
+def _serving_ligands(n, seed=17):
+    """The first n ligands of the serving workload's request stream."""
+    rng = np.random.default_rng(seed)
+    specs = []
+    for k in range(n):
+        a = int(np.exp(rng.uniform(np.log(10), np.log(128.999))))
+        specs.append((a, int(rng.integers(0, 33)), 9000 + k))
+    return make_ligands(specs)
+
+
+def run_batch_96() -> int:
+    """The persistent docking kernel on one 96^3 x 9 receptor of the serving
+    workload (125 MB of z-column quads, about the size of L2): 608 of the
+    serving workload's ligands x 4 runs x 4000 evaluations, two dock_batch
+    calls (for an ncu capture of the second)."""
+    import torch
+
+    from paper_2203_02096_gb300 import capi, synth
+    ctx = capi.Context(0)
+    c = (12.5, -3.25, 7.0)
+    G = capi.grids_from_receptor(ctx, synth.make_receptor(3000, center=c, seed=11), synth.make_box(96, center=c))
+    L = [capi.ligand_from(ctx, l) for l in _serving_ligands(608)]
+    P = capi.default_params(pop_size=150, nruns=4, max_evals=4000, ls_iters=100)
+    for _ in range(2):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        out = capi.dock_batch(ctx, G, L, P, np.arange(len(L), dtype=np.uint64))
+        b.record()
+        torch.cuda.synchronize()
+    ev = int(out["evals"].sum().item())
+    print(json.dumps({"workload": "608 serving ligands x 4 runs x 4000 evaluations, one 96^3 x 9 receptor",
+                      "evals": ev, "seconds": a.elapsed_time(b) / 1e3, "evals_per_s": ev / (a.elapsed_time(b) / 1e3)}),
+          flush=True)
+    for h in L + [G]:
+        h.free()
+    ctx.close()
+    return 0
+
+
+def run_serve_l2() -> int:
+    """Served throughput with every request on one 96^3 x 9 receptor against
+    requests alternating between two (2 x 125 MB of grid copies, twice the
+    L2): 240 of the serving workload's ligands, 20 runs x 60 000 evaluations,
+    all arriving at once, twice each."""
+    from paper_2203_02096_gb300 import capi, serve, synth
+    ctx = capi.Context(0)
+    centers = [(12.5, -3.25, 7.0), (-30.0, 18.0, 4.0)]
+    grids = [capi.grids_from_receptor(ctx, synth.make_receptor(3000, center=c, seed=11 + i), synth.make_box(96, center=c))
+             for i, c in enumerate(centers)]
+    ligs = _serving_ligands(240)
+    server = capi.Server(ctx, capacity=1 << 16, max_atoms=128, pop_max=150)
+    P = capi.default_params(pop_size=150, nruns=20, max_evals=60_000, ls_iters=100)
+    serve.run(ctx, server, grids, [serve.Request(ligs[0], 0, seed=0)], P)
+    out = []
+    for rep in range(2):
+        for name, gi in (("one receptor", lambda k: 0), ("two receptors, alternating", lambda k: k % 2)):
+            reqs = [serve.Request(ligs[k], gi(k), seed=k, arrival=0.0) for k in range(len(ligs))]
+            r = serve.run(ctx, server, grids, reqs, P)
+            ev = sum(int(d.evals.sum()) for d in r.done)
+            out.append({"case": name, "wall_s": r.wall, "evals_per_s": ev / r.wall})
+    server.close()
+    for g in grids:
+        g.free()
+    ctx.close()
+    print(json.dumps({"workload": "240 serving requests x 20 runs x 60k evaluations, all at t = 0", "runs": out}),
+          flush=True)
+    return 0
+
+
 def batched_docking(ctx, dev, n_ligs: int = 1024, nruns: int = 20, full_budget: int = 1_000_000,
                     probe_budget: int = 20_000, n_plain: int = 32, full: bool = True):
     """The batching workload: 1024 ligands with 10-108 atoms and 0-32
@@ -610,12 +679,7 @@ def serving_sweep(ctx, dev, full_budget: int = 500_000, full_rates=((10, 30.0), 
     server = capi.Server(ctx, capacity=1 << 16, max_atoms=128, pop_max=150)
     # request k of every stream: the same ligand (sizes from one seeded draw)
     n_req = max([max(8, int(r * t)) for r, t in full_rates] + [max(8, int(r * probe_seconds)) for r in probe_rates])
-    rng = np.random.default_rng(17)
-    specs = []
-    for k in range(n_req):
-        n = int(np.exp(rng.uniform(np.log(10), np.log(128.999))))
-        specs.append((n, int(rng.integers(0, 33)), 9000 + k))
-    req_ligs = make_ligands(specs)
+    req_ligs = _serving_ligands(n_req)
 
     def stream(rate, seconds, budget, seed):
         n = max(8, int(rate * seconds))
@@ -762,7 +826,7 @@ def pair_list(lig):
 # digest of the kernel sources and input generator it was taken on: the figure
 # is reported only while they are unchanged.
 LS_TRAFFIC_BYTES = 31.04e6
-LS_TRAFFIC_SOURCES = "34859c32270eda0e"
+LS_TRAFFIC_SOURCES = "1b8015fede9db610"
 
 
 # the files that define the local-search kernel and the ligand it runs on
@@ -804,13 +868,17 @@ def main(argv=None):
                     help="side measurements without the full-budget batching and serving runs")
     ap.add_argument("--ls-threads", type=int, default=-1,
                     help="threads per local-search chain (-1 = autotuned, 0 = library default)")
-    ap.add_argument("--only", choices=["score_grad", "batch_small"], default=None,
+    ap.add_argument("--only", choices=["score_grad", "batch_small", "batch_96", "serve_l2"], default=None,
                     help="run one side measurement alone and print its JSON (for profiling)")
     args = ap.parse_args(argv)
     if args.only == "score_grad":
         return run_score_grad_only()
     if args.only == "batch_small":
         return run_batch_small()
+    if args.only == "batch_96":
+        return run_batch_96()
+    if args.only == "serve_l2":
+        return run_serve_l2()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
