@@ -202,11 +202,38 @@ def cpu_sample(w, target_s: float, seed: int = 0):
     P = oracle.make_params(pop_size=w.pop_size, nruns=cores, max_evals=budget, ls_iters=w.ls_iters,
                            ls_rate_pct=w.ls_rate_pct)
     t0 = time.perf_counter()
-    _, _, evals = oracle.dock(lig, grid, P, seed, nthreads=cores)
+    _, best_E, evals = oracle.dock(lig, grid, P, seed, nthreads=cores)
     dt = time.perf_counter() - t0
     desc = (f"{cores} docking runs x {int(evals[0])} evaluations of the drug-size workload (50 runs x 2.5M "
             f"in full), FP64 oracle, one run per thread")
+    _ORACLE_INPUTS["last_sample"] = {"runs": cores, "budget_per_run": budget, "seed": seed, "best_E": best_E,
+                                     "evals": evals}
     return float(evals.sum() / dt), cores, desc, dt
+
+
+def _ks(a, b):
+    a, b = np.sort(a), np.sort(b)
+    xs = np.concatenate([a, b])
+    return float(np.max(np.abs(np.searchsorted(a, xs, side="right") / len(a)
+                               - np.searchsorted(b, xs, side="right") / len(b))))
+
+
+def quality_vs_oracle(ctx, G, L, w):
+    """The GPU docking at the oracle sample's budget, runs and seed: both
+    forms' best energies (the same search, FP32 against FP64), as medians and
+    a two-sample Kolmogorov-Smirnov distance."""
+    from paper_2203_02096_gb300 import capi
+    smp = _ORACLE_INPUTS.get("last_sample")
+    if smp is None:
+        return None
+    P = capi.default_params(pop_size=w.pop_size, nruns=smp["runs"], max_evals=smp["budget_per_run"],
+                            ls_iters=w.ls_iters)
+    _, gE, gev = capi.dock(ctx, G, L, P, smp["seed"])
+    oE = smp["best_E"]
+    return {"runs": smp["runs"], "budget_per_run": smp["budget_per_run"], "seed": smp["seed"],
+            "same_evaluation_counts": bool(np.array_equal(gev, smp["evals"])),
+            "best_E_median": {"gpu": float(np.median(gE)), "oracle": float(np.median(oE))},
+            "best_E_min": {"gpu": float(gE.min()), "oracle": float(oE.min())}, "ks": _ks(gE, oE)}
 
 
 # ---------------------------------------------------------------------------
@@ -343,12 +370,13 @@ def run(args):
     solis = side("solis_wets", lambda: solis_wets_vs_adadelta(ctx, G, L, w, dev, out, value))
     tuning = side("tuning", lambda: tuning_curves(ctx, G, w, tuner, P))
 
-    cpu = None
+    cpu = quality = None
     if rank == 0 and not args.no_cpu:
         t = time.perf_counter()
         v, cores, desc, _ = cpu_sample(w, args.cpu_seconds)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
         section_s["cpu_baseline"] = round(time.perf_counter() - t, 1)
+        quality = quality_vs_oracle(ctx, G, L, w)
 
     if rank == 0:
         line = {
@@ -377,6 +405,7 @@ def run(args):
             "gpu_launches": int(launches),
             "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
             "cpu_baseline": cpu,
+            "quality_vs_oracle": quality,
             "score_grad_batch": batch,
             "batched_docking": multi,
             "serving": serving,

@@ -144,3 +144,25 @@ def test_dock_small_ligand_workload(gpu, oracle_mod):
           f"KS {_ks(bE, oE):.2f}")
     assert abs(np.median(bE) - np.median(oE)) < 0.5, (np.sort(bE), np.sort(oE))
     assert _ks(bE, oE) <= 0.3, (np.sort(bE), np.sort(oE))
+
+
+def test_dock_drug_ligand_workload_distribution(gpu, oracle_mod, drug_system):
+    """The headline workload's ligand and grids (40 atoms / 10 torsions,
+    64^3 x 9 maps, ADADELTA 300 iterations, pop 150) at a reduced budget the
+    oracle finishes in seconds: 16 runs x 100k evaluations through dock() and
+    through orc_dock with the same seed.  Exact evaluation counts; best-energy
+    medians within 0.5 kcal/mol and a two-sample KS distance at most 0.5
+    (about the 2% level for 16 against 16 runs)."""
+    w = drug_system["w"]
+    olig, ogrid = drug_system["olig"], drug_system["grid"]
+    L = capi.ligand_from(gpu, w.ligand)
+    G = capi.grids_from_maps(gpu, drug_system["maps"], w.box)
+    P = _params(pop_size=w.pop_size, nruns=16, max_evals=100_000, ls_iters=w.ls_iters)
+    bg, bE, ev = capi.dock(gpu, G, L, P, 3)
+    og, oE, oev = oracle_mod.dock(olig, ogrid, _oparams(oracle_mod, P), 3)
+    assert np.array_equal(ev, oev)
+    assert np.allclose(bE, olig.score_batch(ogrid, bg, with_grad=False), rtol=1e-9, atol=1e-9)
+    print(f"\ndrug-size docking, 16 runs x 100k: median best E {np.median(bE):.3f} (oracle {np.median(oE):.3f}); "
+          f"KS {_ks(bE, oE):.2f}")
+    assert abs(np.median(bE) - np.median(oE)) < 0.5, (np.sort(bE), np.sort(oE))
+    assert _ks(bE, oE) <= 0.5, (np.sort(bE), np.sort(oE))
