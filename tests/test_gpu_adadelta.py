@@ -23,7 +23,7 @@ import numpy as np
 import pytest
 import torch
 
-from paper_2203_02096_gb300 import capi
+from paper_2203_02096_gb300 import capi, synth
 from tests.tolerances import G_ABS, G_REL, energy_tol, grad_block_errors, grad_tol, gene_blocks
 
 pytestmark = pytest.mark.gpu
@@ -225,3 +225,33 @@ def test_first_step_trajectory(gpu, oracle_mod, drug_system, docked_starts):
         allowed = ratio * gtol + np.spacing(np.abs(x1).astype(np.float32)) + 64 * U32 * np.abs(step)
         assert np.all(np.abs(_diff(xt[b, 1], x1)) <= allowed), (b, np.max(np.abs(_diff(xt[b, 1], x1)) / allowed))
     assert checked >= len(docked_starts) - 2
+
+
+def test_new_entry_points_reject_bad_arguments(gpu, drug_system):
+    """dock_adadelta_step and dock_local_search_trace: argument errors come
+    back as DOCK_ERR_INVALID, an empty batch is a no-op, and the largest
+    genotype (32 torsions, 39 genes) steps like any other."""
+    x = torch.zeros((4, 17), dtype=torch.float32, device="cuda")
+    g, a, b = torch.ones_like(x), torch.zeros_like(x), torch.zeros_like(x)
+    for kw in (dict(rho=1.0), dict(rho=-0.1), dict(eps=0.0)):
+        with pytest.raises(capi.DockError, match="INVALID"):
+            capi.dock_adadelta_step(gpu, x, g, a, b, **kw)
+    bad = torch.zeros((4, 6), dtype=torch.float32, device="cuda")
+    with pytest.raises(capi.DockError, match="INVALID"):
+        capi.dock_adadelta_step(gpu, bad, torch.ones_like(bad), torch.zeros_like(bad), torch.zeros_like(bad))
+    big = torch.zeros((4, 40), dtype=torch.float32, device="cuda")
+    with pytest.raises(capi.DockError, match="INVALID"):
+        capi.dock_adadelta_step(gpu, big, torch.ones_like(big), torch.zeros_like(big), torch.zeros_like(big))
+    empty = torch.zeros((0, 17), dtype=torch.float32, device="cuda")
+    capi.dock_adadelta_step(gpu, empty, empty.clone(), empty.clone(), empty.clone())
+    x39 = torch.zeros((3, 39), dtype=torch.float32, device="cuda")
+    capi.dock_adadelta_step(gpu, x39, torch.ones_like(x39), torch.zeros_like(x39), torch.zeros_like(x39))
+    assert torch.all(x39 < 0)     # a positive gradient moves every gene down
+    L = capi.ligand_from(gpu, drug_system["lig"])
+    G = capi.grids_from_maps(gpu, drug_system["maps"], drug_system["box"])
+    x0 = torch.from_numpy(synth.make_genotypes(2, L.n_torsions, drug_system["box"], seed=1)).cuda()
+    xb, Eb = torch.empty_like(x0), torch.empty(2, device="cuda")
+    xt = torch.empty((2, 3, L.n_genes), device="cuda")
+    rc = gpu.lib.dock_local_search_trace(gpu.h, G.h, L.h, capi._ptr(x0), 2, 3, 0.8, 0.01, 0, capi._ptr(xb),
+                                         capi._ptr(Eb), capi._ptr(xt), None, None, capi._stream(None))
+    assert capi.ERRORS.get(rc) == "DOCK_ERR_INVALID", rc
