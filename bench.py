@@ -653,6 +653,9 @@ def batched_docking(ctx, dev, n_ligs: int = 1024, nruns: int = 20, full_budget: 
         # 21-, 43- and 108-atom ligands of the tuning curves
         Pplain = capi.DockParams.from_buffer_copy(Pf)
         Pplain.ls_threads = 128
+        Pw = capi.DockParams.from_buffer_copy(Pplain)
+        Pw.max_evals = 20_000
+        capi.dock(ctx, G, L[pick[0]], Pw, 0)           # untimed: loads the plain form's kernels
         torch.cuda.synchronize(dev)
         ev_plain, pE = 0, []
         t0 = time.perf_counter()
@@ -734,7 +737,12 @@ def serving_sweep(ctx, dev, full_budget: int = 500_000, full_rates=((10, 30.0), 
             if first is None:
                 first = {d.request.seed: d for d in rep.done}
                 first_reqs = reqs
-        # plain form on the first requests of the first stream
+        # plain form on the first requests of the first stream (one untimed
+        # docking first: the plain form's first call loads its kernels)
+        r0 = first_reqs[0]
+        L0 = capi.ligand_from(ctx, r0.ligand)
+        capi.dock(ctx, grids[r0.grid_index], L0, P, r0.seed)
+        L0.free()
         lat, pE, sE = [], [], []
         t0 = time.perf_counter()
         for r in first_reqs[:n_plain]:
