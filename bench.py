@@ -357,9 +357,11 @@ def run(args):
 
     section_s = {}
 
+    # the side studies and the CPU baseline are single-GPU measurements: a
+    # multi-GPU run (replicas) times the headline only
     def side(name, fn):
         t = time.perf_counter()
-        r = fn() if not args.no_batch else None
+        r = fn() if not args.no_batch and world == 1 else None
         section_s[name] = round(time.perf_counter() - t, 1)
         print(f"[bench] {name}: {section_s[name]} s", file=sys.stderr, flush=True)
         return r
@@ -371,7 +373,7 @@ def run(args):
     tuning = side("tuning", lambda: tuning_curves(ctx, G, w, tuner, P))
 
     cpu = quality = None
-    if rank == 0 and not args.no_cpu:
+    if rank == 0 and world == 1 and not args.no_cpu:
         t = time.perf_counter()
         v, cores, desc, _ = cpu_sample(w, args.cpu_seconds)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
