@@ -690,7 +690,7 @@ def batched_docking(ctx, dev, n_ligs: int = 1024, nruns: int = 20, full_budget: 
 
 def serving_sweep(ctx, dev, full_budget: int = 500_000, full_rates=((10, 30.0), (30, 8.0)),
                   probe_rates=(10, 30, 100, 300, 1000), probe_budget: int = 5_000, probe_seconds: float = 2.0,
-                  nruns: int = 20, n_plain: int = 8, full: bool = True):
+                  nruns: int = 20, n_plain: int = 16, full: bool = True):
     """The serving workload: Poisson arrivals of ligands with 10-128 atoms
     (log-uniform) and 0-32 torsions against two receptors with 96^3 x 9
     maps, 20 runs per request, through the continuous-batching server
