@@ -425,18 +425,23 @@ def run(args):
     return 0
 
 
-def score_grad_throughput(ctx, G, box, dev, reps: int = 5):
+def score_grad_throughput(ctx, G, box, dev, reps: int = 5, score_blocks: int = 0):
     """score_grad_batch over 65536 random genotypes of a 64-atom / 16-torsion
     ligand in the same grids (the differentiation workload): evals/s and the
-    FP32 roofline of that kernel (inputs resident, L2 flushed between calls)."""
+    FP32 roofline of that kernel (inputs resident, L2 flushed between calls).
+    score_blocks > 0 fixes the scorer's register cap instead of tuning it."""
     import torch
 
     from paper_2203_02096_gb300 import autotune, capi, synth
     lig = synth.make_ligand(64, 16, seed=0)
     L = capi.ligand_from(ctx, lig)
-    # register cap of the scorer by the autotuner (untimed)
+    # register cap of the scorer by the autotuner (untimed), unless fixed
     tuner = autotune.Tuner(ctx, path=os.path.join(tempfile.mkdtemp(prefix="dock_tune_"), "tune.json"))
-    blocks = tuner.score_blocks(G, L)
+    if score_blocks > 0:
+        blocks = score_blocks
+        capi.set_option(ctx, capi.OPT_SCORE_BLOCKS, blocks)
+    else:
+        blocks = tuner.score_blocks(G, L)
     genos = torch.from_numpy(synth.make_genotypes(65536, lig.n_torsions, box, seed=0)).to(dev)
     E = torch.empty(65536, device=dev)
     grad = torch.empty_like(genos)
@@ -469,11 +474,13 @@ def score_grad_throughput(ctx, G, box, dev, reps: int = 5):
             "frac_of_measured_ffma": achieved / ffma, "measured_ffma_tflops": ffma,
             "l2_frac_of_measured": grid_bytes_per_eval(lig.n_atoms) * 65536 / t / 1e9 / l2,
             "measured_l2_read_gbs": l2,
-            "autotuned_score_blocks": blocks, "score_blocks_ms": tuner.curve("|score|")}
+            "autotuned_score_blocks": blocks if score_blocks <= 0 else None, "score_blocks": blocks,
+            "score_blocks_ms": tuner.curve("|score|")}
 
 
-def run_score_grad_only() -> int:
-    """The score_grad_batch measurement alone (drug-size grids built on the GPU)."""
+def run_score_grad_only(score_blocks: int = 0) -> int:
+    """The score_grad_batch measurement alone (drug-size grids built on the GPU);
+    score_blocks > 0 fixes the register cap (for profiling one cap)."""
     import torch
 
     from paper_2203_02096_gb300 import capi
@@ -481,7 +488,7 @@ def run_score_grad_only() -> int:
     w = workload()
     ctx = capi.Context(0)
     G = capi.grids_from_receptor(ctx, w.receptor, w.box)
-    print(json.dumps(score_grad_throughput(ctx, G, w.box, dev)), flush=True)
+    print(json.dumps(score_grad_throughput(ctx, G, w.box, dev, score_blocks=score_blocks)), flush=True)
     G.free()
     ctx.close()
     return 0
@@ -909,9 +916,11 @@ def main(argv=None):
                     help="threads per local-search chain (-1 = autotuned, 0 = library default)")
     ap.add_argument("--only", choices=["score_grad", "batch_small", "batch_96", "serve_l2"], default=None,
                     help="run one side measurement alone and print its JSON (for profiling)")
+    ap.add_argument("--score-blocks", type=int, default=0, choices=[0, 1, 6, 8],
+                    help="with --only score_grad: fixed register cap of the scorer (0 = autotuned)")
     args = ap.parse_args(argv)
     if args.only == "score_grad":
-        return run_score_grad_only()
+        return run_score_grad_only(args.score_blocks)
     if args.only == "batch_small":
         return run_batch_small()
     if args.only == "batch_96":

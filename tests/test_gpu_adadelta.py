@@ -227,6 +227,71 @@ def test_first_step_trajectory(gpu, oracle_mod, drug_system, docked_starts):
     assert checked >= len(docked_starts) - 2
 
 
+def _near_reference_starts(olig, box, n, seed):
+    """Starts around the ligand's own conformation (small torsion offsets,
+    random orientation, near the box centre) and two random genotypes of the
+    initial population (deep intramolecular clash)."""
+    rng = np.random.default_rng(seed)
+    centre = (np.asarray(box.box_lo()) + np.asarray(box.box_hi())) / 2
+    X = np.zeros((n, olig.n_genes), np.float32)
+    X[:, 0:3] = centre + rng.uniform(-1.5, 1.5, (n, 3))
+    q = rng.standard_normal((n, 4))
+    X[:, 3:7] = q / np.linalg.norm(q, axis=1, keepdims=True)
+    X[:, 7:] = rng.uniform(-0.4, 0.4, (n, olig.n_torsions))
+    return X
+
+
+@pytest.mark.parametrize("threads", [32, 64, 128, 256])
+@pytest.mark.parametrize("n,t", [(108, 31), (255, 32)])
+def test_chain_large_ligands(gpu, oracle_mod, drug_system, n, t, threads):
+    """The team evaluator at the largest sizes, every team width: a thread
+    places and grid-scores several atoms, each warp runs several pair steps,
+    the torsion tree is 32 lanes deep.  Each iterate of a traced chain is
+    checked against the oracle: energy (stated tolerance at E <= 50, the
+    clash-pose one above), gradient (per block at E <= 50, clash-pose
+    above) where no discontinuity is within reach of FP32 rounding, and the
+    step x_k -> x_{k+1} to FP32 rounding."""
+    lig = synth.make_ligand(n, t, seed=n)
+    olig, ogrid = oracle_mod.OracleLigand(lig), drug_system["grid"]
+    nt, iters = olig.n_torsions, 6
+    starts = np.concatenate([_near_reference_starts(olig, drug_system["box"], 12, seed=n),
+                             oracle_mod.init_population(nt, ogrid, n, 0, 2)])
+    L = capi.ligand_from(gpu, lig)
+    G = capi.grids_from_maps(gpu, drug_system["maps"], drug_system["box"])
+    _, _, xt, gt, Et = capi.dock_local_search_trace(gpu, G, L, torch.from_numpy(starts).cuda(), iters,
+                                                    threads=threads)
+    xt, gt, Et = xt.cpu().numpy(), gt.cpu().numpy().astype(np.float64), Et.cpu().numpy().astype(np.float64)
+    assert np.array_equal(xt[:, 0], starts)
+    n_grad = n_relaxed = 0
+    for b in range(len(starts)):
+        Eo, Go, M = _oracle_at(olig, ogrid, xt[b])
+        F = np.stack([olig.atom_forces(ogrid, x.astype(np.float64))[1] for x in xt[b]])
+        relaxed = Eo <= RELAXED_E_MAX
+        e_ok = M[:, 1] > MARGIN
+        etol = np.where(relaxed, energy_tol(Eo), energy_tol(Eo, F))
+        assert np.all(np.abs(Et[b] - Eo)[e_ok] <= etol[e_ok]), (b, Et[b], Eo)
+        g_ok = (M > MARGIN).all(axis=1)
+        gerr, gtol = grad_block_errors(gt[b], Go, nt)
+        assert np.all((gerr <= gtol)[g_ok & relaxed]), (b, np.argwhere(gerr > gtol)[:4])
+        clash = g_ok & ~relaxed
+        assert np.all(np.abs(gt[b] - Go).max(axis=1)[clash] <= grad_tol(Go)[clash]), b
+        n_grad += int(g_ok.sum())
+        n_relaxed += int((g_ok & relaxed).sum())
+        Eg2, Edx2 = np.zeros(7 + nt), np.zeros(7 + nt)
+        for k in range(iters - 1):
+            xp, Eg2, Edx2 = oracle_mod.adadelta_step(xt[b, k], gt[b, k], Eg2, Edx2, nt, rho=np.float32(0.8),
+                                                     eps=np.float32(1e-2))
+            allowed = (2 * np.spacing(np.abs(xp).astype(np.float32)).astype(np.float64)
+                       + (16 + 4 * k + k * k) * U32 * np.abs(_diff(xp, xt[b, k])))
+            assert np.all(np.abs(_diff(xt[b, k + 1], xp)) <= allowed), (b, k)
+    # a 255-atom pose has ~760 coordinates and ~32k pairs: two thirds of its
+    # iterates have an atom within 1e-4 A of a cell face or a pair that close
+    # to the cutoff (a fifth at 108 atoms); enough others remain
+    assert n_grad >= len(starts) * iters // 5, n_grad
+    print(f"\n{n} atoms / {t} torsions, {threads} threads: {n_grad} of {len(starts) * iters} iterates "
+          f"gradient-checked ({n_relaxed} at E <= {RELAXED_E_MAX})")
+
+
 def test_new_entry_points_reject_bad_arguments(gpu, drug_system):
     """dock_adadelta_step and dock_local_search_trace: argument errors come
     back as DOCK_ERR_INVALID, an empty batch is a no-op, and the largest
