@@ -211,6 +211,68 @@ def cpu_sample(w, target_s: float, seed: int = 0):
     return float(evals.sum() / dt), cores, desc, dt
 
 
+def cpu_other_workloads(head):
+    """The FP64 oracle as it stands on the other workloads, on this host's
+    cores (maps built by the oracle, untimed):
+    - small-ligand docking (16 atoms / 4 torsions, 40^3 x 7 maps, 10 runs x
+      100k evaluations) in full;
+    - score+grad of the 65536-genotype batch of a 64-atom / 16-torsion ligand
+      in the drug-size grids, in full;
+    - the batching mix (10-108 atoms, 0-32 torsions, 80^3 x 9 maps) and the
+      serving mix (10-128 atoms log-uniform, 0-32 torsions; on the same
+      80^3 maps, the serving workload's 96^3 maps not being built here):
+      16 of the workload's own ligands spread over the size range, one
+      docking of `cores` runs x ~3300 evaluations each (three generations),
+      extrapolated to 20 runs x 1M (batching) and 20 runs x 500k (serving)
+      evaluations per ligand."""
+    import oracle
+
+    from paper_2203_02096_gb300 import synth
+    cores = os.cpu_count() or 1
+    out = {"cores": cores, "kind": "oracle"}
+    w1 = synth.small_ligand_workload()
+    g1 = oracle.OracleGrid(oracle.build_maps(w1.receptor, w1.box, nthreads=cores).astype(np.float32), w1.box)
+    P = oracle.make_params(pop_size=w1.pop_size, nruns=w1.nruns, max_evals=w1.max_evals, ls_iters=w1.ls_iters,
+                           ls_rate_pct=w1.ls_rate_pct)
+    t0 = time.perf_counter()
+    _, _, ev = oracle.dock(oracle.OracleLigand(w1.ligand), g1, P, w1.seed, nthreads=cores)
+    dt = time.perf_counter() - t0
+    out["small_ligand_docking"] = {"workload": w1.name, "in_full": True, "seconds": dt,
+                                   "evals_per_s": float(ev.sum()) / dt, "ligands_per_hour": 3600.0 / dt,
+                                   "threads": min(cores, w1.nruns)}
+    grid = _ORACLE_INPUTS[head.name][0]
+    lig = synth.make_ligand(64, 16, seed=0)
+    X = synth.make_genotypes(65536, lig.n_torsions, head.box, seed=0)
+    t0 = time.perf_counter()
+    oracle.OracleLigand(lig).score_batch(grid, X, with_grad=True, nthreads=cores)
+    dt = time.perf_counter() - t0
+    out["score_grad_batch"] = {"workload": "65536 genotypes, 64 atoms / 16 torsions, 64^3 x 9 maps", "in_full": True,
+                               "seconds": dt, "evals_per_s": 65536 / dt}
+    box = synth.make_box(80)
+    g3 = oracle.OracleGrid(oracle.build_maps(synth.make_receptor(3000, seed=4), box,
+                                             nthreads=cores).astype(np.float32), box)
+    mixes = {"batching": (_batching_specs(1024), 1_000_000), "serving": (_serving_specs(1024), 500_000)}
+    P = oracle.make_params(pop_size=150, nruns=cores, max_evals=3000, ls_iters=100)
+    for name, (specs, full_budget) in mixes.items():
+        order = np.argsort([n for n, _, _ in specs], kind="stable")
+        pick = order[np.linspace(0, len(specs) - 1, 16).round().astype(int)]
+        ligs = [oracle.OracleLigand(synth.make_ligand(*specs[k][:2], seed=specs[k][2])) for k in pick]
+        evals = 0
+        t0 = time.perf_counter()
+        for k, ol in zip(pick, ligs):
+            _, _, ev = oracle.dock(ol, g3, P, int(k), nthreads=cores)
+            evals += int(ev.sum())
+        dt = time.perf_counter() - t0
+        rate = evals / dt
+        out[name] = {"workload": f"{name} ligand mix, 80^3 x 9 maps", "in_full": False,
+                     "sample": f"16 of its ligands ({specs[pick[0]][0]}-{specs[pick[-1]][0]} atoms, every "
+                               f"64th by size) x {cores} runs x {int(evals / 16 / cores)} evaluations",
+                     "seconds": dt, "evals_per_s": rate,
+                     "ligands_per_hour_extrapolated": 3600.0 * rate / (20 * full_budget),
+                     "extrapolated_to": f"20 runs x {full_budget} evaluations per ligand"}
+    return out
+
+
 def _ks(a, b):
     a, b = np.sort(a), np.sort(b)
     xs = np.concatenate([a, b])
@@ -379,6 +441,10 @@ def run(args):
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
         section_s["cpu_baseline"] = round(time.perf_counter() - t, 1)
         quality = quality_vs_oracle(ctx, G, L, w)
+        if not args.no_batch:
+            t = time.perf_counter()
+            cpu["other_workloads"] = cpu_other_workloads(w)
+            section_s["cpu_other_workloads"] = round(time.perf_counter() - t, 1)
 
     if rank == 0:
         line = {
@@ -523,14 +589,27 @@ def run_batch_small() -> int:
     return 0
 
 
-def _serving_ligands(n, seed=17):
-    """The first n ligands of the serving workload's request stream."""
+def _serving_specs(n, seed=17):
+    """(atoms, torsions, seed) of the first n ligands of the serving
+    workload's request stream: atoms log-uniform in [10, 128]."""
     rng = np.random.default_rng(seed)
     specs = []
     for k in range(n):
         a = int(np.exp(rng.uniform(np.log(10), np.log(128.999))))
         specs.append((a, int(rng.integers(0, 33)), 9000 + k))
-    return make_ligands(specs)
+    return specs
+
+
+def _serving_ligands(n, seed=17):
+    """The first n ligands of the serving workload's request stream."""
+    return make_ligands(_serving_specs(n, seed))
+
+
+def _batching_specs(n):
+    """(atoms, torsions, seed) of the batching workload's ligands: 10-108
+    atoms and 0-32 torsions, uniform."""
+    rng = np.random.default_rng(3)
+    return [(int(rng.integers(10, 109)), int(rng.integers(0, 33)), 5000 + k) for k in range(n)]
 
 
 def run_batch_96() -> int:
@@ -608,8 +687,7 @@ def batched_docking(ctx, dev, n_ligs: int = 1024, nruns: int = 20, full_budget: 
     import torch
 
     from paper_2203_02096_gb300 import autotune, capi, synth
-    rng = np.random.default_rng(3)
-    ligs = make_ligands([(int(rng.integers(10, 109)), int(rng.integers(0, 33)), 5000 + k) for k in range(n_ligs)])
+    ligs = make_ligands(_batching_specs(n_ligs))
     box = synth.make_box(80)
     G = capi.grids_from_receptor(ctx, synth.make_receptor(3000, seed=4), box)
     L = [capi.ligand_from(ctx, l) for l in ligs]
