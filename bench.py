@@ -432,6 +432,7 @@ def run(args):
     multi = side("batched_docking", lambda: batched_docking(ctx, dev, full=not args.quick))
     serving = side("serving", lambda: serving_sweep(ctx, dev, full=not args.quick))
     solis = side("solis_wets", lambda: solis_wets_vs_adadelta(ctx, G, L, w, dev, out, value))
+    graphs = side("cuda_graph", lambda: graph_vs_direct(ctx, G, L, P, dev))
     tuning = side("tuning", lambda: tuning_curves(ctx, G, w, tuner, P))
 
     cpu = quality = None
@@ -478,6 +479,7 @@ def run(args):
             "batched_docking": multi,
             "serving": serving,
             "solis_wets": solis,
+            "cuda_graph": graphs,
             "tuning": tuning,
             "best_energy_median": float(np.median(out["best_E"].cpu().numpy())),
             "side_section_seconds": section_s,
@@ -879,6 +881,68 @@ def tuning_curves(ctx, G, w, tuner, P_head):
         lig.free()
     return {"ls_threads_curve": out, "headline_ls_threads": int(P_head.ls_threads),
             "headline_tuning_ms": tuner.curve("|ls|")}
+
+
+def graph_vs_direct(ctx, G, L, P_head, dev, reps: int = 3):
+    """The plain docking replayed as a CUDA graph against direct launches.
+    dock_async_noalloc (no allocation, no host synchronisation) is captured
+    once per workload and replayed; both forms run the same seed, so they do
+    the same work.  Milliseconds per docking (CUDA events, no L2 flush), for
+    the drug-size workload and the small-ligand one (shorter kernels, where
+    the gaps between launches weigh more)."""
+    import torch
+
+    from paper_2203_02096_gb300 import capi, synth
+
+    def outputs(R, Gn):
+        return dict(best_geno=torch.empty((R, Gn), dtype=torch.float32, device=dev),
+                    best_E32=torch.empty(R, dtype=torch.float32, device=dev),
+                    best_E=torch.empty(R, dtype=torch.float64, device=dev),
+                    evals=torch.empty(R, dtype=torch.int64, device=dev))
+
+    def timed(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize(dev)
+        return a.elapsed_time(b) / reps
+
+    def one(Gr, Lg, P):
+        out = outputs(P.nruns, Lg.n_genes)
+        side = torch.cuda.Stream(dev)
+        side.wait_stream(torch.cuda.current_stream(dev))
+        with torch.cuda.stream(side):
+            capi.dock_async_noalloc(ctx, Gr, Lg, P, 123, out)
+        torch.cuda.current_stream(dev).wait_stream(side)
+        torch.cuda.synchronize(dev)
+        n0 = ctx.launch_count()
+        direct = timed(lambda: capi.dock_async_noalloc(ctx, Gr, Lg, P, 123, out))
+        launches = (ctx.launch_count() - n0) // reps
+        ref = {k: v.clone() for k, v in out.items()}
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            capi.dock_async_noalloc(ctx, Gr, Lg, P, 123, out)
+        graph.replay()
+        torch.cuda.synchronize(dev)
+        same = all(torch.equal(out[k], ref[k]) for k in ref)
+        replay = timed(graph.replay)
+        del graph
+        return {"direct_ms": direct, "graph_ms": replay, "launches_per_docking": int(launches),
+                "graph_same_results": bool(same)}
+
+    res = {"note": "same seed in both forms; no L2 flush; ms per docking"}
+    res["drug_size"] = one(G, L, P_head)
+    w1 = synth.small_ligand_workload()
+    G1 = capi.grids_from_receptor(ctx, w1.receptor, w1.box)
+    L1 = capi.ligand_from(ctx, w1.ligand)
+    P1 = capi.default_params(pop_size=w1.pop_size, nruns=w1.nruns, max_evals=w1.max_evals, ls_iters=w1.ls_iters)
+    capi.dock(ctx, G1, L1, P1, 0)       # loads the kernels at this ligand's shapes
+    res["small_ligand"] = one(G1, L1, P1)
+    L1.free()
+    G1.free()
+    return res
 
 
 def solis_wets_vs_adadelta(ctx, G, L, w, dev, ada_out, ada_value):

@@ -344,6 +344,11 @@ int server_destroy(dock_server *srv);
  *    threads -- race on it; serialise them.
  *  - It runs the ADADELTA local search only: ls_method != 0 fails with
  *    DOCK_ERR_INVALID.
+ *  - It makes no host synchronisation either, and its launch sequence is
+ *    fixed by the parameters, so a call can be captured into a CUDA graph
+ *    (stream capture) and replayed; a replay recomputes the captured seed's
+ *    docking into the same output pointers.  Capture after a first direct
+ *    call with the same ligand, so that every kernel is loaded.
  * Outputs and arguments as dock_async. */
 #define DOCK_NOALLOC_SCRATCH_BYTES (8u << 20)
 int dock_async_noalloc(dock_ctx *ctx, const dock_grids *grids, const dock_ligand *lig, const dock_params *params,
