@@ -422,8 +422,16 @@ def run(args):
     # the side studies and the CPU baseline are single-GPU measurements: a
     # multi-GPU run (replicas) times the headline only
     def side(name, fn):
+        # a failing side study is reported in its section, not fatal to the
+        # headline line
         t = time.perf_counter()
-        r = fn() if not args.no_batch and world == 1 else None
+        r = None
+        if not args.no_batch and world == 1:
+            try:
+                r = fn()
+            except Exception as exc:  # noqa: BLE001
+                torch.cuda.synchronize(dev)
+                r = {"error": f"{type(exc).__name__}: {exc}"}
         section_s[name] = round(time.perf_counter() - t, 1)
         print(f"[bench] {name}: {section_s[name]} s", file=sys.stderr, flush=True)
         return r
