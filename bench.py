@@ -785,7 +785,7 @@ def batched_docking(ctx, dev, n_ligs: int = 1024, nruns: int = 20, full_budget: 
 
 def serving_sweep(ctx, dev, full_budget: int = 500_000, full_rates=((10, 30.0), (30, 8.0)),
                   probe_rates=(10, 30, 100, 300, 1000), probe_budget: int = 5_000, probe_seconds: float = 2.0,
-                  nruns: int = 20, n_plain: int = 16, full: bool = True):
+                  nruns: int = 20, n_plain: int = 16, full: bool = True, light_seconds: float = 8.0):
     """The serving workload: Poisson arrivals of ligands with 10-128 atoms
     (log-uniform) and 0-32 torsions against two receptors with 96^3 x 9
     maps, 20 runs per request, through the continuous-batching server
@@ -797,7 +797,8 @@ def serving_sweep(ctx, dev, full_budget: int = 500_000, full_rates=((10, 30.0), 
       arrival rate); the plain
       form (one dock() per request, in order) on the first n_plain requests
       of the rate-10 stream, with the best energies of the same requests in
-      both forms;
+      both forms; light load (2 per second for light_seconds) served only
+      and with serve.run's idle_plain route;
     - the knee at a reduced budget: every probe rate for probe_seconds."""
     import torch
 
@@ -851,11 +852,20 @@ def serving_sweep(ctx, dev, full_budget: int = 500_000, full_rates=((10, 30.0), 
             pE.append(e)
             sE.append(first[r.seed].best_E)
         t_plain = time.perf_counter() - t0
+        # light load: 2 requests/s, served only and with the plain route for
+        # requests that find the GPU idle (the library's team width; the
+        # plain form's kernels are loaded by the dockings above)
+        light = {}
+        for mode, idle in (("served_only", False), ("idle_plain", True)):
+            rep = serve.run(ctx, server, grids, stream(2, light_seconds, full_budget, 2), P, timeout=900.0,
+                            idle_plain=idle)
+            light[mode] = rep.summary()
         res["full_budget"] = {
             "budget_per_run": full_budget, "sweep": sweep,
             "plain": {"requests": n_plain, "requests_per_s": n_plain / t_plain,
                       "ligands_per_hour": 3600.0 * n_plain / t_plain, "latency_s_median": float(np.median(lat))},
-            "best_E_median_same_requests": {"served": float(np.median(sE)), "plain": float(np.median(pE))}}
+            "best_E_median_same_requests": {"served": float(np.median(sE)), "plain": float(np.median(pE))},
+            "light_load": {"rate_per_s": 2, "arrival_seconds": light_seconds, **light}}
     # the knee at a reduced budget
     Pp = capi.default_params(pop_size=150, nruns=nruns, max_evals=probe_budget, ls_iters=100)
     knee = []

@@ -48,3 +48,30 @@ def test_results_same_alone_in_the_mix_and_batched(gpu, drug_system):
     lat = mixed.latencies()
     assert np.all(np.isfinite(lat)) and np.all(lat > 0)
     server.close()
+
+
+def test_idle_plain_route_gives_the_served_results(gpu, drug_system):
+    """With idle_plain and one-warp plain teams, requests that find the GPU
+    idle dock in the plain form; their results equal dock_batch's (and so
+    the served ones) bit for bit, so the route does not change a request's
+    answer.  A burst that queues past the bound goes to the persistent
+    kernel."""
+    G0 = capi.grids_from_maps(gpu, drug_system["maps"], drug_system["box"])
+    P = capi.default_params(pop_size=40, nruns=4, max_evals=2500, ls_iters=10)
+    server = capi.Server(gpu, capacity=1024, max_atoms=128, pop_max=150)
+    reqs = [serve.Request(_ligand(k), 0, seed=31 * k + 1, arrival=0.5 * k) for k in range(4)]
+    burst = [serve.Request(_ligand(10 + k), 0, seed=7 * k + 5, arrival=2.5) for k in range(8)]
+    rep = serve.run(gpu, server, [G0], reqs + burst, P, idle_plain=True, plain_queue=4, plain_threads=32)
+    assert len(rep.done) == 12
+    by_seed = {d.request.seed: d for d in rep.done}
+    assert all(by_seed[r.seed].route == "plain" for r in reqs)
+    assert sum(by_seed[r.seed].route == "served" for r in burst) >= 7
+    for r in reqs[:2] + burst[:2]:
+        L = capi.ligand_from(gpu, r.ligand)
+        out = capi.dock_batch(gpu, G0, [L], P, np.array([r.seed], np.uint64))
+        torch.cuda.synchronize()
+        d = by_seed[r.seed]
+        assert np.array_equal(out["best_geno"][0, :, :L.n_genes].cpu().numpy(), d.best_geno), d.route
+        assert np.array_equal(out["best_E"][0].cpu().numpy(), d.best_E), d.route
+        assert np.array_equal(out["evals"][0].cpu().numpy(), d.evals), d.route
+    server.close()

@@ -142,3 +142,103 @@ def test_steady_throughput_counts_completions_while_requests_arrive():
     # a stream shorter than a second of overlap has no steady rate
     short = serve.ServiceReport(done=rep.done[:1], wall=5.0)
     assert short.steady_throughput() is None
+
+
+class FakePlain:
+    """A plain-form docking that finishes after a fixed number of polls."""
+    started = []
+    polls = 3
+
+    def __init__(self, ctx, grids, lig, params, seed):
+        self.lig, self.params, self.left = lig, params, FakePlain.polls
+        FakePlain.started.append((lig.name, params.ls_threads))
+
+    def done(self):
+        self.left -= 1
+        return self.left <= 0
+
+    def result(self):
+        R = self.params.nruns
+        return (np.full((R, self.lig.n_genes), -1.0, np.float32), np.full(R, -7.0), np.full(R, 100, np.int64))
+
+
+@pytest.fixture
+def fake_plain(monkeypatch):
+    FakePlain.started, FakePlain.polls = [], 3
+    monkeypatch.setattr(serve, "PlainDocking", FakePlain)
+    yield
+
+
+def _spaced(n, gap):
+    return [serve.Request({"name": k, "torsions": 3, "bytes": 1 << 20}, 0, seed=k, arrival=k * gap) for k in range(n)]
+
+
+def test_idle_gpu_requests_take_the_plain_route(fake_capi, fake_plain):
+    """Requests that arrive one at a time, each after the previous one is
+    done, are all docked in the plain form with the asked team width;
+    nothing reaches the server."""
+    params = capi.default_params(nruns=4, ls_threads=128)
+    srv = FakeServer(capacity=64)
+    rep = serve.run(None, srv, [None], _spaced(6, 0.02), params, poll_sleep=1e-4, timeout=30.0, idle_plain=True,
+                    plain_threads=32)
+    assert [d.route for d in rep.done] == ["plain"] * 6
+    assert [n for n, _ in FakePlain.started] == list(range(6))
+    assert all(t == 32 for _, t in FakePlain.started)
+    assert params.ls_threads == 128                   # the caller's parameters are untouched
+    assert srv.order == [] and FakeLigand.live == 0
+    assert rep.summary()["plain_route"] == 6
+    assert all(d.best_geno.shape == (4, 10) and np.all(d.best_E == -7.0) for d in rep.done)
+
+
+def test_a_short_queue_waits_for_the_plain_slot_a_long_one_goes_to_the_server(fake_capi, fake_plain):
+    params = capi.default_params(nruns=2)
+    # three at once: the first docks plain, two wait for it (queue <= 4)
+    srv = FakeServer(capacity=64)
+    FakePlain.polls = 3
+    rep = serve.run(None, srv, [None], _spaced(3, 0.0), params, poll_sleep=1e-4, timeout=30.0, idle_plain=True)
+    assert sorted(d.route for d in rep.done) == ["plain"] * 3 and srv.order == []
+    # one request, then nineteen more while it docks plain: the queue (19 >
+    # 4) goes to the persistent kernel, in arrival order, once the plain
+    # docking is done (the two never share the GPU)
+    FakePlain.started, FakePlain.polls = [], 400     # the plain docking outlasts the arrivals
+    reqs = _spaced(20, 0.0)
+    for r in reqs[1:]:
+        r.arrival = 0.005
+    srv = FakeServer(capacity=64, polls_to_finish=5)
+    submit, plain_done = srv.submit, []
+
+    def watched_submit(grids, lig, p, seed):
+        assert plain_done, "a server submission beside a running plain docking"
+        return submit(grids, lig, p, seed)
+
+    srv.submit = watched_submit
+    done = FakePlain.done
+
+    def watched_done(self):
+        d = done(self)
+        if d:
+            plain_done.append(True)
+        return d
+
+    FakePlain.done = watched_done
+    try:
+        rep = serve.run(None, srv, [None], reqs, params, poll_sleep=1e-4, timeout=30.0, idle_plain=True,
+                        plain_queue=4)
+    finally:
+        FakePlain.done = done
+    routes = {d.request.ligand["name"]: d.route for d in rep.done}
+    assert len(routes) == 20 and routes[0] == "plain"
+    assert all(routes[k] == "served" for k in range(1, 20))
+    assert srv.order == list(range(1, 20))
+    # twenty at once: the queue is long from the start, all are served
+    FakePlain.started, FakePlain.polls = [], 3
+    srv = FakeServer(capacity=64, polls_to_finish=5)
+    rep = serve.run(None, srv, [None], _spaced(20, 0.0), params, poll_sleep=1e-4, timeout=30.0, idle_plain=True)
+    assert [d.route for d in rep.done] == ["served"] * 20 and FakePlain.started == []
+    assert FakeLigand.live == 0
+
+
+def test_idle_plain_needs_adadelta(fake_capi, fake_plain):
+    params = capi.default_params(nruns=2, ls_method=1)
+    with pytest.raises(ValueError):
+        serve.run(None, FakeServer(capacity=8), [None], _spaced(1, 0.0), params, idle_plain=True)
